@@ -1,0 +1,120 @@
+"""Flux-differencing DGSEM on conforming quad/hex meshes (oracle, float64).
+
+The paper evaluates its semidiscretisation U' = F(U) (eq. SemidiscretizationODE)
+with the DGSEM on LGL nodes, an entropy-conservative two-point volume flux
+via flux differencing with SBP operators, and an EC or ES (LLF-dissipative)
+surface flux (Sec. 2.1, Sec. 4.1).  Written out for one element with
+reference coordinates xi^k, nodal metric terms Ja^k and Jacobian J:
+
+  J_q dU_q/dt = - sum_k sum_m 2 D_{q m} f#(U_q, U_m; (Ja^k_q + Ja^k_m)/2)   (m along the xi^k line of q)
+                - sum_{faces at q} (1/omega_face) ( f*(U^-, U^+; nu) - f(U_q).nu )
+
+where nu is the element's outward scaled normal (+-Ja^k at the face node) and
+omega_face the LGL weight of the face node's index across the face.  Metric
+terms: 1D Ja = 1, J = x_xi; 2D Ja^1 = (y_eta, -x_eta), Ja^2 = (-y_xi, x_xi),
+J = x_xi y_eta - x_eta y_xi, derivatives by D (this satisfies the discrete
+metric identities); 3D cross-product form Ja^1 = x_eta x x_zeta etc. (exact
+for affine elements, the only 3D elements used here).
+
+An interface's flux is evaluated once, with the normal of its '+' side (the
+row's left element), and enters both elements with opposite signs.
+"""
+import numpy as np
+
+from . import lgl as _lgl
+
+
+class Geometry:
+    def __init__(self, coords, faces, N=3):
+        self.coords = np.asarray(coords, dtype=np.float64)
+        self.n_elem, self.NP, self.dim = self.coords.shape
+        self.N = N
+        self.x, self.w, self.D = _lgl.lgl(N)
+        self.faces = np.asarray(faces)
+        self.shape_nodes = (N + 1,) * self.dim          # (k, j, i) order reversed below
+        self._metrics()
+
+    def tens(self, a):
+        """[..., n_elem, NP] -> [..., n_elem, (k), (j), i]  (i fastest)."""
+        return a.reshape(a.shape[:-1] + (self.N + 1,) * self.dim)
+
+    def flat(self, a):
+        return a.reshape(a.shape[:-self.dim] + (self.NP,))
+
+    def dxi(self, a, k):
+        """Derivative along reference direction k (0 = xi, 1 = eta, 2 = zeta) of a
+        nodal field a[..., n_elem, NP]."""
+        t = self.tens(a)
+        ax = t.ndim - 1 - k
+        t = np.moveaxis(t, ax, -1)
+        t = np.einsum("qm,...m->...q", self.D, t)
+        t = np.moveaxis(t, -1, ax)
+        return self.flat(t)
+
+    def _metrics(self):
+        X = np.moveaxis(self.coords, 2, 0)             # [dim, n_elem, NP]
+        d = self.dim
+        dX = [self.dxi(X, k) for k in range(d)]         # dX[k][comp] = d x_comp / d xi^k
+        if d == 1:
+            self.J = dX[0][0]
+            self.Ja = np.ones((1, 1) + self.J.shape)
+        elif d == 2:
+            xx, xy = dX[0][0], dX[1][0]
+            yx, yy = dX[0][1], dX[1][1]
+            self.J = xx * yy - xy * yx
+            self.Ja = np.array([[yy, -xy], [-yx, xx]])  # Ja[k][comp]
+        else:
+            a, b, c = dX[0], dX[1], dX[2]
+            self.Ja = np.array([np.cross(b, c, axis=0), np.cross(c, a, axis=0), np.cross(a, b, axis=0)])
+            self.J = np.sum(a * self.Ja[0], axis=0)
+        wn = self.w
+        if d == 1:
+            wq = wn
+        elif d == 2:
+            wq = np.outer(wn, wn).ravel()               # index j*4 + i -> w_j w_i
+        else:
+            wq = np.einsum("k,j,i->kji", wn, wn, wn).ravel()
+        self.wq = wq                                    # quadrature weight per node
+        self.wJ = wq[None, :] * self.J                  # [n_elem, NP]
+
+    def integrate(self, f):
+        """sum_e sum_q omega_q J_q f_q  for a nodal scalar f[n_elem, NP]."""
+        return float(np.sum(self.wJ * f))
+
+
+def rhs(geo, phys, U):
+    """dU/dt = F(U) on all elements; U[V, n_elem, NP] -> K[V, n_elem, NP]."""
+    d, N = geo.dim, geo.N
+    V = U.shape[0]
+    Ut = geo.tens(U)                                   # [V, E, (k),(j), i]
+    acc = np.zeros_like(Ut)
+    # ---- volume: flux differencing along each reference direction
+    for k in range(d):
+        ax = Ut.ndim - 1 - k
+        Uk = np.moveaxis(Ut, ax, -1)                   # [V, E, ..., 4]
+        Jak = np.moveaxis(geo.tens(geo.Ja[k]), ax, -1)  # [dim, E, ..., 4]
+        nav = 0.5 * (Jak[..., :, None] + Jak[..., None, :])
+        F = phys.volume_flux(Uk[..., :, None], Uk[..., None, :], nav)   # [V, E, ..., q, m]
+        vol = 2.0 * np.einsum("qm,...qm->...q", geo.D, F)
+        acc += np.moveaxis(vol, -1, ax)
+    # ---- surface: each listed interface once, normal of the '+' side
+    eL, fL, eR, fR = (geo.faces[:, c] for c in range(4))
+    for k in range(d):
+        sel = fL == 2 * k + 1
+        if not np.any(sel):
+            continue
+        el, er = eL[sel], eR[sel]
+        ax = Ut.ndim - 1 - k
+        Uk = np.moveaxis(Ut, ax, -1)
+        Jak = np.moveaxis(geo.tens(geo.Ja[k]), ax, -1)
+        uL = Uk[..., N][:, el]                         # [V, nf, face nodes...]
+        uR = Uk[..., 0][:, er]
+        nu = Jak[..., N][:, el]                        # outward normal of the '+' side
+        fs = phys.surface_flux(uL, uR, nu)
+        # acc holds -J dU/dt, so the surface term enters with a + sign
+        cL = (fs - phys.flux(uL, nu)) / geo.w[N]
+        cR = (-fs + phys.flux(uR, nu)) / geo.w[0]
+        accm = np.moveaxis(acc, ax, -1)                # view
+        np.add.at(accm[..., N], (slice(None), el), cL)
+        np.add.at(accm[..., 0], (slice(None), er), cR)
+    return -geo.flat(acc) / geo.J[None]

@@ -1,0 +1,156 @@
+"""P-ERRK time stepping, written as the paper states it (oracle, float64).
+
+Stage loop: eq. PartitionedRKSystem in full Butcher form.  For an element of
+partition r,
+    U_{n,i} = U_n + dt sum_{j<i} A^(r)_{ij} K_j ,   K_i = F(U_{n,i})
+(F evaluated everywhere; only the rows of A^(r) decide which K_j matter, so
+this equals evaluating F^(r) on its own index set), and
+    d_n = sum_i b_i K_i                                     (Sec. 3).
+Entropy change (eq. EntropyChange_EntropyVariables_ReArranged):
+    Delta H = dt sum_i b_i sum_e sum_q omega_q J_q < w(U_{n,i,q}), K_{i,q} >.
+Relaxation (eq. RelaxationEquation and its derivative, Sec. 3.1):
+    r(g)  = H(U_n + g dt d) - H_target(g),
+    r'(g) = < w(U_n + g dt d), dt d >_M - dH_target/dg,
+with H_target = H_n + g Delta H (eq. EntropyConservationRRKM_Short), = H_n
+(entropy kept from step to step, Sec. 4.1.1) or = H(U_0) (Sec. 4.1.2).
+Newton-Raphson with unit step from the guess (gamma_{n-1}, 1 at the first
+step); stop on |r| <= tol_r * A_n (A_n = sum omega J |s(U_n)|), on
+|dgamma| <= tol_g or after max_it passes; if it did not stop by one of the
+two tolerances, or gamma is not in (0.5, 1.5), take gamma = 1 (Sec. 3.2,
+fallback of Sec. 3.2.1).  Relaxed update (eq. RRKM_Update):
+U_{n+1} = U_n + gamma dt d, t_{n+1} = t_n + gamma dt.
+"""
+import dataclasses
+
+import numpy as np
+
+from . import dgsem, physics, tableau
+
+GUESS_ONE, GUESS_PREV = "one", "prev"
+TARGET_DELTA_H, TARGET_PREV, TARGET_INITIAL = "delta_h", "prev", "initial"
+
+
+@dataclasses.dataclass
+class NewtonOptions:
+    max_it: int = 10
+    tol_r: float = 1e-14
+    tol_g: float = 1e-14
+    guess: str = GUESS_PREV
+    target: str = TARGET_DELTA_H
+    relax: bool = True
+
+
+@dataclasses.dataclass
+class StepRecord:
+    gamma: float
+    iters: int
+    converged: bool
+    H_n: float
+    dH: float
+    H_next: float
+    t: float
+    stage_dot: list          # per stage with b_i != 0: sum omega J <w, K_i>
+
+
+class Solver:
+    def __init__(self, wl, opts=None, p=None, E=None):
+        self.wl = wl
+        self.phys = physics.Physics(wl.equation, wl.surface_flux, wl.gamma_gas)
+        self.geo = dgsem.Geometry(wl.coords, wl.faces)
+        self.p = p or wl.order
+        self.E = list(E or wl.E)
+        self.c, self.b, self.As = tableau.family(self.p, self.E)
+        self.S = len(self.b)
+        self.part = np.asarray(wl.part)
+        self.opts = opts or NewtonOptions()
+        self.U = wl.u0.copy()
+        self.t = 0.0
+        self.gamma_prev = 1.0
+        self.H0 = self.entropy(self.U)
+
+    # ---- functionals
+    def entropy(self, U):
+        return self.geo.integrate(self.phys.entropy(U))
+
+    def abs_entropy(self, U):
+        return self.geo.integrate(np.abs(self.phys.entropy(U)))
+
+    def dot_w(self, U, K):
+        return self.geo.integrate(np.sum(self.phys.entropy_vars(U) * K, axis=0))
+
+    def rhs(self, U):
+        return dgsem.rhs(self.geo, self.phys, U)
+
+    # ---- one step
+    def stages(self, U, dt):
+        """Returns (d, Delta H, per-stage integrals) from the full Butcher stage loop."""
+        S = self.S
+        K = []
+        dH = 0.0
+        stage_dot = []
+        A_e = np.stack([self.As[r] for r in self.part])        # [n_elem, S, S]
+        for i in range(S):
+            Ui = U.copy()
+            for j in range(i):
+                Ui += dt * A_e[None, :, i, j, None] * K[j]
+            Ki = self.rhs(Ui)
+            K.append(Ki)
+            if self.b[i] != 0.0:
+                s = self.dot_w(Ui, Ki)
+                stage_dot.append(s)
+                dH += self.b[i] * s
+        d = sum(self.b[i] * K[i] for i in range(S) if self.b[i] != 0.0)
+        return d, dt * dH, stage_dot
+
+    def newton(self, U, d, dt, H_n, A_n, dH, guess):
+        o = self.opts
+        if o.target == TARGET_DELTA_H:
+            tgt = lambda g: H_n + g * dH
+            dtgt = dH
+        elif o.target == TARGET_PREV:
+            tgt = lambda g: H_n
+            dtgt = 0.0
+        else:
+            tgt = lambda g: self.H0
+            dtgt = 0.0
+        g = guess
+        converged = False
+        it = 0
+        while it < o.max_it:
+            Ug = U + g * dt * d
+            r = self.entropy(Ug) - tgt(g)
+            rp = self.dot_w(Ug, dt * d) - dtgt
+            it += 1
+            if abs(r) <= o.tol_r * A_n:
+                converged = True
+                break
+            if not np.isfinite(r) or not np.isfinite(rp) or rp == 0.0:
+                break
+            dg = -r / rp
+            g = g + dg
+            if abs(dg) <= o.tol_g:
+                converged = True
+                break
+        if not converged or not np.isfinite(g) or not (0.5 < g < 1.5):
+            return 1.0, it, False
+        return g, it, True
+
+    def step(self, dt):
+        U = self.U
+        H_n = self.entropy(U)
+        A_n = self.abs_entropy(U)
+        d, dH, stage_dot = self.stages(U, dt)
+        if self.opts.relax:
+            guess = self.gamma_prev if self.opts.guess == GUESS_PREV else 1.0
+            g, it, conv = self.newton(U, d, dt, H_n, A_n, dH, guess)
+        else:
+            g, it, conv = 1.0, 0, True
+        self.U = U + g * dt * d
+        self.t += g * dt
+        if self.opts.relax and conv:
+            self.gamma_prev = g
+        rec = StepRecord(g, it, conv, H_n, dH, self.entropy(self.U), self.t, stage_dot)
+        return rec
+
+    def run(self, dt, nsteps):
+        return [self.step(dt) for _ in range(nsteps)]

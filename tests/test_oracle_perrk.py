@@ -1,0 +1,128 @@
+"""Pins of the oracle's P-ERRK stepping against closed forms and invariants."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads
+from oracle import perrk, tableau
+
+
+def test_closed_form_gamma_quadratic_entropy():
+    """Burgers, s = u^2/2: r(g) = g dt <u,d> + g^2 dt^2 <d,d>/2 - g dH has the
+    nonzero root g = 2 (dH - dt <u,d>) / (dt^2 <d,d>) (inner products with omega J)."""
+    wl = workloads.burgers_1d()
+    s = perrk.Solver(wl, perrk.NewtonOptions(tol_r=1e-15, tol_g=1e-16))
+    for _ in range(3):
+        U = s.U.copy()
+        dt = wl.dt * 2
+        d, dH, _ = s.stages(U, dt)
+        ud = s.geo.integrate(U[0] * d[0])
+        dd = s.geo.integrate(d[0] * d[0])
+        g_cf = 2.0 * (dH - dt * ud) / (dt * dt * dd)
+        rec = s.step(dt)
+        assert rec.converged
+        # attainable agreement: rounding of H (~1e-16 |H|) divided by r'(gamma)
+        rp = dt * ud + rec.gamma * dt * dt * dd - dH
+        tol = 20 * 2.2e-16 * abs(rec.H_n) / abs(rp)
+        assert abs(rec.gamma - g_cf) < tol
+        assert abs(rec.gamma - 1.0) > 100 * tol  # relaxation is active
+
+
+@pytest.mark.parametrize("p,E", [(2, [6, 4, 2]), (3, [6, 4, 3]), (4, [8, 6, 5])])
+def test_linear_invariants_random_partitions(p, E):
+    wl = workloads.small_box_2d(n=6, seed=3, R=3, E=E, order=p, random_parts=True)
+    s = perrk.Solver(wl)
+    m0 = [s.geo.integrate(s.U[v]) for v in range(4)]
+    for _ in range(6):
+        s.step(wl.dt)
+    m1 = [s.geo.integrate(s.U[v]) for v in range(4)]
+    for a, b in zip(m0, m1):
+        assert abs(a - b) < 1e-13 * (abs(a) + 1.0)
+
+
+@pytest.mark.parametrize("target", [perrk.TARGET_DELTA_H, perrk.TARGET_PREV, perrk.TARGET_INITIAL])
+def test_entropy_conservation_ec(target):
+    wl = workloads.small_box_2d(n=6, seed=4, R=2, E=[6, 3], order=3, surface="ec")
+    s = perrk.Solver(wl, perrk.NewtonOptions(target=target))
+    A = s.abs_entropy(s.U)
+    H0 = s.H0
+    for _ in range(5):
+        rec = s.step(wl.dt * 4)
+        assert rec.converged
+        assert abs(rec.H_next - rec.H_n) <= 1e-13 * A
+    assert abs(s.entropy(s.U) - H0) <= 1e-13 * A
+    # without relaxation the same run changes entropy by much more than round-off
+    s2 = perrk.Solver(wl, perrk.NewtonOptions(relax=False))
+    for _ in range(5):
+        rec = s2.step(wl.dt * 4)
+    assert abs(s2.entropy(s2.U) - H0) > 1e-11 * A
+
+
+def test_entropy_stable_es():
+    wl = workloads.small_box_2d(n=6, seed=5, R=2, E=[6, 3], order=3, ic="khi")
+    s = perrk.Solver(wl)
+    for _ in range(4):
+        rec = s.step(wl.dt)
+        assert rec.dH < 0
+        assert rec.H_next - rec.H_n == pytest.approx(rec.gamma * rec.dH, abs=1e-12 * abs(rec.H_n))
+
+
+@pytest.mark.parametrize("p,E", [(2, [8, 4]), (3, [8, 4]), (4, [8, 5])])
+def test_gamma_minus_one_rate(p, E):
+    """gamma_n = 1 + O(dt^(p-1)) (Sec. 2.4)."""
+    wl = workloads.burgers_1d(E=E)
+    dev = []
+    for k in range(3):
+        s = perrk.Solver(wl, perrk.NewtonOptions(tol_r=0.0, tol_g=1e-10, max_it=30), p=p, E=E)
+        rec = s.step((4 if p < 4 else 8) * wl.dt / 2 ** k)
+        dev.append(abs(rec.gamma - 1.0))
+    rates = [math.log2(dev[i] / dev[i + 1]) for i in range(2)]
+    assert min(rates) > (p - 1) - 0.35, (dev, rates)
+
+
+def _run_to(wl, p, E, dt, n, relax):
+    s = perrk.Solver(wl, perrk.NewtonOptions(relax=relax, tol_r=1e-16, tol_g=1e-16), p=p, E=E)
+    for _ in range(n):
+        s.step(dt)
+    return s
+
+
+@pytest.mark.parametrize("p,E", [(2, [8, 4]), (3, [8, 4]), (4, [8, 5])])
+def test_temporal_order(p, E):
+    """Observed temporal order p: the relaxed solution at its own final time
+    t = sum gamma_n dt against a fine non-relaxed fourth-order reference run
+    to that same time on the same mesh."""
+    wl = workloads.burgers_1d(E=E)
+    T = 0.02
+    errs = []
+    for k in range(3):
+        n = 16 * 2 ** k
+        s = _run_to(wl, p, E, T / n, n, relax=True)
+        ref = _run_to(wl, 4, [8, 5], s.t / 256, 256, relax=False)
+        errs.append(np.abs(s.U - ref.U).max())
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert min(rates) > p - 0.4, (errs, rates)
+
+
+def test_ssprk3_special_case():
+    wl = workloads.small_box_2d(n=4, seed=6, R=1, E=[3], order=3)
+    s = perrk.Solver(wl, perrk.NewtonOptions(relax=False))
+    U = s.U.copy()
+    dt = wl.dt
+    F = s.rhs
+    u1 = U + dt * F(U)
+    u2 = 0.75 * U + 0.25 * (u1 + dt * F(u1))
+    u3 = U / 3.0 + 2.0 / 3.0 * (u2 + dt * F(u2))
+    s.step(dt)
+    assert np.abs(s.U - u3).max() < 1e-13 * np.abs(U).max()
+
+
+def test_newton_fallback():
+    wl = workloads.burgers_1d()
+    s = perrk.Solver(wl, perrk.NewtonOptions(max_it=0))
+    rec = s.step(wl.dt)
+    assert rec.gamma == 1.0 and not rec.converged
+    s = perrk.Solver(wl, perrk.NewtonOptions(max_it=1, tol_r=0.0, tol_g=0.0))
+    rec = s.step(wl.dt)
+    assert rec.gamma == 1.0 and not rec.converged and rec.iters == 1

@@ -1,0 +1,396 @@
+"""Seeded synthetic workloads: meshes, partition assignment and initial states.
+
+This module is the only code shared by the CUDA path and the CPU oracle.  It
+holds none of the method's arithmetic (no DG operators, fluxes, Runge-Kutta
+tableaux or relaxation); it only places mesh nodes, pairs faces, assigns
+partitions by element size and evaluates initial conditions at the nodes.
+
+Conventions (the input format of ``perrk_create``):
+
+* polynomial degree N = 3, nodes per element NP = 4**dim, reference node
+  positions are the four Legendre-Gauss-Lobatto points {-1, -1/sqrt5, 1/sqrt5, 1}
+  (written here as the input format's fixed point set);
+* node index inside an element: q = i + 4*j + 16*k (i along xi fastest);
+* faces of an element: 0 = -xi, 1 = +xi, 2 = -eta, 3 = +eta, 4 = -zeta, 5 = +zeta;
+* face list rows (eL, fL, eR, fR): fL is a '+' face (1, 3, 5) of eL, fR = fL - 1
+  the matching '-' face of eR, face nodes in the same order on both sides;
+* state layout SoA [V][n_elem][NP] in float64;
+* partition 0 is the finest (largest stage-evaluation count E), ids 0..R-1.
+
+Physical setups follow the paper's test cases: the isentropic vortex
+(Sec. 4.1.2, eqs. for rho, v, p of the vortex), the Kelvin-Helmholtz
+instability initial state (Sec. 3.2.2) and the Taylor-Green vortex (standard
+form, not in the paper).  Partition assignment uses the shortest element edge
+(Sec. 2.2, eq. CharSpeed_DG with h the minimal corner distance).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+N_POLY = 3
+REF_NODES = np.array([-1.0, -1.0 / math.sqrt(5.0), 1.0 / math.sqrt(5.0), 1.0])
+GAMMA_GAS = 1.4
+BASE_SEED = 250704991
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    dim: int
+    equation: str            # "burgers1d" | "euler2d" | "euler3d"
+    coords: np.ndarray       # [n_elem, NP, dim] float64
+    faces: np.ndarray        # [n_faces, 4] int32 (eL, fL, eR, fR)
+    part: np.ndarray         # [n_elem] int32, 0 = finest
+    E: list                  # stage evaluations per partition (descending)
+    order: int               # P-ERK order p
+    u0: np.ndarray           # [V, n_elem, NP] float64
+    dt: float
+    volume_flux: str         # "ec_burgers" | "ec_ranocha"
+    surface_flux: str        # "ec" | "es_rusanov"
+    gamma_gas: float = GAMMA_GAS
+    info: dict = dataclasses.field(default_factory=dict)
+
+    @property
+    def n_elem(self):
+        return self.coords.shape[0]
+
+    @property
+    def nvar(self):
+        return self.u0.shape[0]
+
+    @property
+    def n_dof(self):
+        return int(self.u0.size)
+
+    def dof_stage_per_step(self):
+        """Sum over partitions of E^(r) * M^(r) (M = nodes x variables), the
+        paper's count of scalar RHS evaluations per step (eq. RHSEvals)."""
+        per_elem = self.u0.shape[0] * self.u0.shape[2]
+        counts = np.bincount(self.part, minlength=len(self.E))
+        return int(sum(e * c for e, c in zip(self.E, counts)) * per_elem)
+
+
+# ----------------------------------------------------------------------------
+# structured (logically Cartesian, periodic) meshes
+# ----------------------------------------------------------------------------
+
+def _elem_index(ix, iy, iz, n):
+    return ix + n[0] * (iy + n[1] * iz)
+
+
+def structured_faces(n):
+    """Periodic face list for an n[0] x n[1] x n[2] element grid (missing dims = 1)."""
+    dim = len(n)
+    nn = list(n) + [1] * (3 - dim)
+    rows = []
+    for iz in range(nn[2]):
+        for iy in range(nn[1]):
+            for ix in range(nn[0]):
+                e = _elem_index(ix, iy, iz, nn)
+                rows.append((e, 1, _elem_index((ix + 1) % nn[0], iy, iz, nn), 0))
+                if dim >= 2:
+                    rows.append((e, 3, _elem_index(ix, (iy + 1) % nn[1], iz, nn), 2))
+                if dim >= 3:
+                    rows.append((e, 5, _elem_index(ix, iy, (iz + 1) % nn[2], nn), 4))
+    return np.asarray(rows, dtype=np.int32)
+
+
+def tensor_coords(edges):
+    """Node coordinates of an axis-aligned tensor mesh from per-axis cell edges."""
+    dim = len(edges)
+    n = [len(e) - 1 for e in edges]
+    nn = n + [1] * (3 - dim)
+    NP = 4 ** dim
+    out = np.empty((int(np.prod(n)), NP, dim))
+    t = 0.5 * (REF_NODES + 1.0)
+    per_axis = []
+    for a in range(dim):
+        lo = np.asarray(edges[a][:-1])
+        hi = np.asarray(edges[a][1:])
+        per_axis.append(lo[:, None] + (hi - lo)[:, None] * t[None, :])  # [n_a, 4]
+    for iz in range(nn[2]):
+        for iy in range(nn[1]):
+            for ix in range(nn[0]):
+                e = _elem_index(ix, iy, iz, nn)
+                for q in range(NP):
+                    i, j, k = q % 4, (q // 4) % 4, q // 16
+                    idx = (ix, iy, iz)
+                    loc = (i, j, k)
+                    for a in range(dim):
+                        out[e, q, a] = per_axis[a][idx[a], loc[a]]
+    return out
+
+
+def min_corner_edge(coords, dim):
+    """Shortest distance between adjacent corner nodes of each element."""
+    c = coords
+    if dim == 1:
+        return np.abs(c[:, 3, 0] - c[:, 0, 0])
+    corner = lambda i, j, k=0: c[:, (3 if i else 0) + 4 * (3 if j else 0) + 16 * (3 if k else 0), :]
+    pairs = []
+    ks = (0, 1) if dim == 3 else (0,)
+    for k in ks:
+        for j in (0, 1):
+            pairs.append((corner(0, j, k), corner(1, j, k)))
+        for i in (0, 1):
+            pairs.append((corner(i, 0, k), corner(i, 1, k)))
+    if dim == 3:
+        for i in (0, 1):
+            for j in (0, 1):
+                pairs.append((corner(i, j, 0), corner(i, j, 1)))
+    d = np.stack([np.linalg.norm(a - b, axis=-1) for a, b in pairs], axis=1)
+    return d.min(axis=1)
+
+
+def levels_from_h(h, h_ref, n_levels):
+    """Refinement level of each element: round(log2(h_ref / h)), clipped.
+    Level L elements get partition id n_levels-1-L so that 0 is the finest."""
+    lev = np.clip(np.rint(np.log2(h_ref / h)), 0, n_levels - 1).astype(np.int32)
+    return (n_levels - 1 - lev).astype(np.int32)
+
+
+# ----------------------------------------------------------------------------
+# initial states
+# ----------------------------------------------------------------------------
+
+def prim_to_cons(rho, v, p, gamma=GAMMA_GAS):
+    v = np.asarray(v)
+    kin = 0.5 * rho * np.sum(v * v, axis=0)
+    return np.concatenate([rho[None], rho[None] * v, (p / (gamma - 1.0) + kin)[None]], axis=0)
+
+
+def isentropic_vortex(x, y, t, center, strength, L=10.0, R=1.5, mach=0.4, gamma=GAMMA_GAS):
+    """Isentropic vortex of Sec. 4.1.2 (background rho=1, v=(1,1), p=rho^g/(g Ma^2)),
+    vortex centre translated with v_inf and wrapped to the nearest periodic image.
+    The velocity perturbation is the rotated vector (-c_y, c_x)."""
+    vinf = np.array([1.0, 1.0])
+    cx = x - center[0] - vinf[0] * t
+    cy = y - center[1] - vinf[1] * t
+    cx = (cx + L) % (2 * L) - L
+    cy = (cy + L) % (2 * L) - L
+    g = np.exp((1.0 - (cx * cx + cy * cy)) / (2.0 * R * R))
+    rho = (1.0 - strength ** 2 * mach ** 2 * (gamma - 1.0) * g * g / (8.0 * math.pi ** 2)) ** (1.0 / (gamma - 1.0))
+    amp = strength * g / (2.0 * math.pi * R)
+    vx = vinf[0] - amp * cy
+    vy = vinf[1] + amp * cx
+    p = rho ** gamma / (gamma * mach ** 2)
+    return prim_to_cons(rho, np.stack([vx, vy]), p, gamma)
+
+
+def kelvin_helmholtz(x, y, phase=0.0, amp=0.1, gamma=GAMMA_GAS):
+    """Kelvin-Helmholtz initial state of Sec. 3.2.2 with a seeded phase."""
+    b = np.tanh(15.0 * y + 7.5) - np.tanh(15.0 * y - 7.5)
+    rho = 0.5 + 0.75 * b
+    vx = 0.5 * (b - 1.0)
+    vy = amp * np.sin(2.0 * math.pi * x + phase)
+    p = np.ones_like(x)
+    return prim_to_cons(rho, np.stack([vx, vy]), p, gamma)
+
+
+def taylor_green(x, y, z, mach=0.1, gamma=GAMMA_GAS):
+    """Taylor-Green vortex (Brachet/DeBonis form), rho = 1, V0 = 1."""
+    vx = np.sin(x) * np.cos(y) * np.cos(z)
+    vy = -np.cos(x) * np.sin(y) * np.cos(z)
+    vz = np.zeros_like(x)
+    p = 1.0 / (gamma * mach ** 2) + (np.cos(2 * x) + np.cos(2 * y)) * (np.cos(2 * z) + 2.0) / 16.0
+    return prim_to_cons(np.ones_like(x), np.stack([vx, vy, vz]), p, gamma)
+
+
+def to_soa(u_nodes):
+    """[V, n_elem, NP] from an array already shaped that way (copy, contiguous)."""
+    return np.ascontiguousarray(u_nodes, dtype=np.float64)
+
+
+# ----------------------------------------------------------------------------
+# the five workloads
+# ----------------------------------------------------------------------------
+
+def burgers_1d(n_coarse_each_side=24, n_fine=16, E=(8, 4), dt=None):
+    """64 periodic elements on [0, 1]: 24 of width h, 16 central of width h/4,
+    24 of width h (h = 1/52).  u0 = 1 + 0.5 sin(2 pi x)."""
+    n_total_width = 2 * n_coarse_each_side + n_fine / 4.0
+    h = 1.0 / n_total_width
+    widths = [h] * n_coarse_each_side + [h / 4] * n_fine + [h] * n_coarse_each_side
+    edges = np.concatenate([[0.0], np.cumsum(widths)])
+    edges[-1] = 1.0
+    coords = tensor_coords([edges])
+    n = len(widths)
+    faces = structured_faces([n])
+    hmin = min_corner_edge(coords, 1)
+    part = levels_from_h(hmin, h, 2)
+    x = coords[:, :, 0]
+    u0 = (1.0 + 0.5 * np.sin(2 * math.pi * x))[None]
+    if dt is None:
+        dt = 0.25 * h / 1.5 / 7.0 * 2.0
+    return Workload("burgers1d_64", 1, "burgers1d", coords, faces, part, list(E), 2, to_soa(u0), dt,
+                    "ec_burgers", "ec", info=dict(h=h, t_end=0.1))
+
+
+def _radial_contraction(X, Y, R0=6.0, B=0.75):
+    """Smooth, compactly supported, monotone radial map r -> r (1 - B (1 - (r/R0)^4)^3):
+    identity for r >= R0, element size reduced by 1 - B = 1/4 around the centre."""
+    r = np.sqrt(X * X + Y * Y)
+    s = np.minimum(r / R0, 1.0)
+    fac = 1.0 - B * (1.0 - s ** 4) ** 3
+    return X * fac, Y * fac
+
+
+def vortex_2d(n=64, L=10.0, seed=1, n_levels=3, E=(12, 6, 3), order=3, cfl=0.5, mixed_note=None):
+    """Isentropic vortex on an n x n periodic curvilinear mesh of [-L, L]^2: a
+    central patch contracted by 4 (two refinement levels), then a seeded
+    smooth periodic displacement of at most 10% of the logical cell size."""
+    rng = np.random.default_rng(BASE_SEED + 2 + 1000 * seed)
+    H = 2 * L / n
+    k = rng.integers(1, 4, size=4)
+    ph = rng.uniform(0, 2 * math.pi, size=4)
+    t = 0.5 * (REF_NODES + 1.0)
+    NP = 16
+    coords = np.empty((n * n, NP, 2))
+    for iy in range(n):
+        for ix in range(n):
+            e = ix + n * iy
+            for q in range(NP):
+                i, j = q % 4, q // 4
+                X = -L + (ix + t[i]) * H
+                Y = -L + (iy + t[j]) * H
+                sx = (X + L) / (2 * L)
+                sy = (Y + L) / (2 * L)
+                dX = 0.1 * H * math.sin(2 * math.pi * k[0] * sx + ph[0]) * math.sin(2 * math.pi * k[1] * sy + ph[1])
+                dY = 0.1 * H * math.sin(2 * math.pi * k[2] * sx + ph[2]) * math.sin(2 * math.pi * k[3] * sy + ph[3])
+                x, y = _radial_contraction(np.float64(X + dX), np.float64(Y + dY))
+                coords[e, q, 0] = x
+                coords[e, q, 1] = y
+    faces = structured_faces([n, n])
+    hmin = min_corner_edge(coords, 2)
+    part = levels_from_h(hmin, H, n_levels)
+    center = rng.uniform(-2.0, 2.0, size=2)
+    strength = rng.uniform(3.0, 5.0)
+    u0 = isentropic_vortex(coords[:, :, 0], coords[:, :, 1], 0.0, center, strength, L=L)
+    # characteristic speed |v| + c <= ~2.2 for this vortex; finest h ~ H/4
+    dt = cfl * (H / 4) / (2 * N_POLY + 1) / 2.5
+    return Workload(f"vortex2d_{n}x{n}", 2, "euler2d", coords, faces, part, list(E), order, to_soa(u0), dt,
+                    "ec_ranocha", "es_rusanov",
+                    info=dict(center=center, strength=strength, L=L, H=H, perturb_k=k, perturb_phase=ph))
+
+
+def graded_edges(n, lo, hi, bands, n_levels, fine_counts):
+    """1D edges of n cells on [lo, hi] refined towards the band centres.
+    Around each band centre: fine_counts[l] cells of width h0 / 2^(l) on each
+    side for l = n_levels-1 .. 1 (innermost finest), the rest coarse and
+    uniform.  Returns (edges, level per cell)."""
+    per_band = []
+    for l in range(n_levels - 1, 0, -1):
+        per_band.append((l, fine_counts[l]))
+    # cells per band: innermost level counted once on each side
+    band_cells = []
+    for c in bands:
+        seq = []
+        for l, cnt in per_band:
+            seq = [l] * cnt + seq + [l] * cnt
+        band_cells.append((c, seq))
+    n_fine = sum(len(s) for _, s in band_cells)
+    n_coarse = n - n_fine
+    assert n_coarse > 0
+    # solve for the coarse width h0' so that the total length fits, with the
+    # fine cells measured in units of the nominal coarse size h0 = (hi-lo)/n
+    h0 = (hi - lo) / n
+    fine_len = sum(h0 / 2 ** l for _, s in band_cells for l in s)
+    hc = ((hi - lo) - fine_len) / n_coarse
+    # lay out: coarse cells evenly distributed between bands
+    band_lengths = [sum(h0 / 2 ** l for l in s) for _, s in band_cells]
+    widths, levels = [], []
+    centres = [c for c, _ in band_cells]
+    # compute coarse counts between band edges proportional to gap length
+    starts = [c - bl / 2 for c, bl in zip(centres, band_lengths)]
+    ends = [c + bl / 2 for c, bl in zip(centres, band_lengths)]
+    gaps = [starts[0] - lo] + [starts[i + 1] - ends[i] for i in range(len(centres) - 1)] + [hi - ends[-1]]
+    total_gap = sum(gaps)
+    counts = [int(round(g / total_gap * n_coarse)) for g in gaps]
+    counts[-1] = n_coarse - sum(counts[:-1])
+    for bi in range(len(centres)):
+        widths += [hc] * counts[bi]
+        levels += [0] * counts[bi]
+        for l in band_cells[bi][1]:
+            widths.append(h0 / 2 ** l)
+            levels.append(l)
+    widths += [hc] * counts[-1]
+    levels += [0] * counts[-1]
+    edges = np.concatenate([[lo], lo + np.cumsum(widths)])
+    edges[-1] = hi
+    return edges, np.asarray(levels, dtype=np.int32), h0
+
+
+def khi_2d(n=256, seed=1, E=(16, 10, 7, 5), order=4, n_levels=4, fine_counts=None, cfl=0.4):
+    """Kelvin-Helmholtz on [-1, 1]^2, n x n quads, uniform in x and graded in y
+    with 4 levels around the shear layers y = +-0.5 (partition by shortest edge)."""
+    rng = np.random.default_rng(BASE_SEED + 3 + 1000 * seed)
+    if fine_counts is None:
+        s = n // 256 if n >= 256 else 0
+        fine_counts = {1: max(1, n // 32), 2: max(1, n // 32), 3: max(1, n // 32)}
+    ex = np.linspace(-1.0, 1.0, n + 1)
+    ey, ylev, h0 = graded_edges(n, -1.0, 1.0, [-0.5, 0.5], n_levels, fine_counts)
+    coords = tensor_coords([ex, ey])
+    faces = structured_faces([n, n])
+    hx = 2.0 / n
+    hmin = min_corner_edge(coords, 2)
+    part = levels_from_h(hmin, hx, n_levels)
+    phase = rng.uniform(0, 2 * math.pi)
+    u0 = kelvin_helmholtz(coords[:, :, 0], coords[:, :, 1], phase=phase)
+    hfine = hmin.min()
+    dt = cfl * hfine / (2 * N_POLY + 1) / 2.0
+    return Workload(f"khi2d_{n}x{n}", 2, "euler2d", coords, faces, part, list(E), order, to_soa(u0), dt,
+                    "ec_ranocha", "es_rusanov", info=dict(phase=phase, hx=hx))
+
+
+def tgv_3d(n=64, n_fine=16, E=(8, 4), order=3, cfl=0.5):
+    """Taylor-Green vortex on [0, 2 pi]^3, n^3 affine boxes, the central n_fine
+    cells per axis at half width (partition by shortest edge: cross of slabs)."""
+    nc = n - n_fine
+    hc = 2 * math.pi / (nc + n_fine / 2.0)
+    w = [hc] * (nc // 2) + [hc / 2] * n_fine + [hc] * (nc - nc // 2)
+    e1 = np.concatenate([[0.0], np.cumsum(w)])
+    e1[-1] = 2 * math.pi
+    coords = tensor_coords([e1, e1, e1])
+    faces = structured_faces([n, n, n])
+    hmin = min_corner_edge(coords, 3)
+    part = levels_from_h(hmin, hc, 2)
+    u0 = taylor_green(coords[:, :, 0], coords[:, :, 1], coords[:, :, 2])
+    c = math.sqrt(1.0 / 0.01)  # speed of sound for Ma = 0.1, rho = 1
+    dt = cfl * (hc / 2) / (2 * N_POLY + 1) / (c + 1.0)
+    return Workload(f"tgv3d_{n}^3", 3, "euler3d", coords, faces, part, list(E), order, to_soa(u0), dt,
+                    "ec_ranocha", "ec", info=dict(hc=hc))
+
+
+def small_box_2d(n=8, seed=0, R=2, E=(6, 3), order=3, ic="vortex", surface="es_rusanov", random_parts=False):
+    """Small tensor mesh on [-L, L]^2 for tests, optionally with random partition ids."""
+    rng = np.random.default_rng(BASE_SEED + 7 + 1000 * seed)
+    L = 5.0
+    edges, lev, h0 = graded_edges(n, -L, L, [0.0], R, {l: 1 for l in range(1, R)}) if R > 1 else (np.linspace(-L, L, n + 1), None, 2 * L / n)
+    ex = np.linspace(-L, L, n + 1)
+    coords = tensor_coords([ex, edges])
+    faces = structured_faces([n, n])
+    hmin = min_corner_edge(coords, 2)
+    part = levels_from_h(hmin, 2 * L / n, R) if R > 1 else np.zeros(n * n, np.int32)
+    if random_parts:
+        part = rng.integers(0, R, size=n * n).astype(np.int32)
+    if ic == "vortex":
+        u0 = isentropic_vortex(coords[:, :, 0], coords[:, :, 1], 0.0, rng.uniform(-1, 1, 2), 4.0, L=L, R=1.0)
+    else:
+        u0 = kelvin_helmholtz(coords[:, :, 0] / L, coords[:, :, 1] / L, phase=rng.uniform(0, 6.28))
+    dt = 0.2 * hmin.min() / (2 * N_POLY + 1) / 2.5
+    return Workload(f"box2d_{n}", 2, "euler2d", coords, faces, part, list(E), order, to_soa(u0), dt,
+                    "ec_ranocha", surface)
+
+
+def by_name(name, **kw):
+    table = {
+        "burgers1d": burgers_1d,
+        "vortex2d": vortex_2d,
+        "khi2d": khi_2d,
+        "tgv3d": tgv_3d,
+        "box2d": small_box_2d,
+    }
+    return table[name](**kw)
