@@ -1,0 +1,226 @@
+/*
+ * perrk.h -- C ABI of the GB300 P-ERRK multirate stage-loop library (libperrk.so).
+ *
+ * The library advances a DGSEM semidiscretisation U' = F(U) (Sec. 2.1 of
+ * arXiv 2507.04991, eq. SemidiscretizationODE) with a Paired Explicit
+ * Relaxation Runge-Kutta (P-ERRK) method:
+ *   - partitioned P-ERK stage loop, F evaluated only on the elements of the
+ *     partitions active at each stage (Sec. 2.2, eq. PartitionedRKSystem and
+ *     the example after eq. PERK_ButcherTableauClassic_p2_E36);
+ *   - direction d = sum_i b_i K_i and entropy change
+ *     Delta H = dt sum_i b_i <w(U_{n,i}), K_i>_M (Sec. 3, eq.
+ *     EntropyChange_EntropyVariables_ReArranged);
+ *   - Newton solve of r(gamma) = H(U_n + gamma dt d) - H_n - gamma Delta H = 0
+ *     (eq. RelaxationEquation, Sec. 3.1) and the relaxed update
+ *     U_{n+1} = U_n + gamma dt d, t_{n+1} = t_n + gamma dt (eq. RRKM_Update).
+ *
+ * Conventions shared by all calls
+ *   - polynomial degree N = 3 on Legendre-Gauss-Lobatto nodes; NP = 4^dim
+ *     nodes per element, node index q = i + 4 j + 16 k (i along xi fastest);
+ *   - state layout SoA [V][n_elem][NP] float64, V = 1 (Burgers) or dim + 2
+ *     (Euler: rho, rho v, rho E);
+ *   - faces of an element: 0 = -xi, 1 = +xi, 2 = -eta, 3 = +eta, 4 = -zeta,
+ *     5 = +zeta; a face row (eL, fL, eR, fR) pairs the '+' face fL of eL with
+ *     the '-' face fR = fL - 1 of eR, face nodes in the same order on both
+ *     sides (logically structured, possibly periodic, conforming meshes);
+ *   - every device call is enqueued on the caller's CUDA stream (a
+ *     cudaStream_t passed as void*, NULL = legacy default stream);
+ *   - all entry points return perrk_status; nothing is thrown across the ABI.
+ *
+ * Ownership: the library allocates and frees its own device buffers
+ * (perrk_create*, perrk_destroy).  Caller pointers are only read or written
+ * during the call (or the work it enqueues) and are never retained.
+ */
+#ifndef PERRK_H
+#define PERRK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PERRK_OK = 0,
+    PERRK_INVALID_ARG = 1,       /* malformed mesh / tableau / options; nothing allocated */
+    PERRK_CUDA_ERROR = 2,        /* a CUDA runtime call failed; see perrk_last_error() */
+    PERRK_NONPHYSICAL_STATE = 3, /* rho <= 0, p <= 0 or non-finite values were met */
+    PERRK_TIMEOUT = 4,           /* a bounded device wait expired */
+    PERRK_OUT_OF_MEMORY = 5,
+    PERRK_NOT_SUPPORTED = 6
+} perrk_status;
+
+typedef enum { PERRK_BURGERS_1D = 0, PERRK_EULER_1D = 1, PERRK_EULER_2D = 2, PERRK_EULER_3D = 3 } perrk_equation;
+typedef enum { PERRK_VOLUME_EC = 0 } perrk_volume_flux;          /* Burgers (a^2+ab+b^2)/6 or Ranocha's EC/KEP flux */
+typedef enum { PERRK_SURFACE_EC = 0, PERRK_SURFACE_ES_RUSANOV = 1 } perrk_surface_flux;
+typedef enum { PERRK_FP64 = 0, PERRK_MIXED = 1 } perrk_precision;
+typedef enum { PERRK_GUESS_ONE = 0, PERRK_GUESS_PREV = 1, PERRK_GUESS_MLP = 2 } perrk_guess;
+typedef enum { PERRK_TARGET_DELTA_H = 0, PERRK_TARGET_PREV = 1, PERRK_TARGET_INITIAL = 2 } perrk_target;
+
+/* Step-status flags (perrk_step_info.flags), OR-ed over the steps of a call. */
+#define PERRK_FLAG_NEWTON_FALLBACK 0x1u   /* Newton did not converge: gamma = 1 taken (Sec. 3.2.1) */
+#define PERRK_FLAG_NONPHYSICAL     0x2u   /* rho <= 0 or p <= 0 met at some node */
+#define PERRK_FLAG_NONFINITE       0x4u   /* NaN / Inf met */
+
+/* Mesh (Sec. 2.2: elements carry a partition id r in 0..R-1). */
+typedef struct {
+    int dim;                      /* 1, 2 or 3 */
+    int N;                        /* polynomial degree; must be 3 */
+    int n_elem;
+    const double *node_coords;    /* host, [n_elem][NP][dim]: physical LGL node positions */
+    int n_faces;                  /* must equal n_elem * dim (every element has one '+' face per direction) */
+    const int32_t *faces;         /* host, [n_faces][4] = (eL, fL, eR, fR) as above */
+    const int32_t *partition_id;  /* host, [n_elem], values in 0..R-1 */
+} perrk_mesh_desc;
+
+/* P-ERK family in low-storage form (Sec. 2.2, appendix A archetypes): the
+ * stage-i row of partition r is U_{n,i} = U_n + dt (a1[r][i] K_1 + asub[r][i] K_{i-1}).
+ * Member r evaluates F at stage 1 and at stages S - E[r] + 2 .. S; at every other
+ * stage its row must be (c_i, 0), and at its first active stage after stage 1
+ * asub must be 0.  c and b are shared by all members (eq. InternalConsistency:
+ * a1 + asub = c_i; eq. Conservation: one b).  b_i != 0 only at stages where all
+ * members are active. */
+typedef struct {
+    int order;                    /* p: 2, 3 or 4 (minimum E: 2, 3, 5) */
+    int S;                        /* stages, = max E */
+    int R;                        /* partitions */
+    const int32_t *E;             /* host, [R] stage evaluations per member */
+    const double *c;              /* host, [S] */
+    const double *b;              /* host, [S] */
+    const double *a1;             /* host, [R][S] coefficient of K_1 (row i = index i, 0-based) */
+    const double *asub;           /* host, [R][S] coefficient of K_{i-1} */
+    int equation;                 /* perrk_equation */
+    double gamma_gas;             /* ratio of specific heats (Euler), e.g. 1.4 */
+    int volume_flux;              /* perrk_volume_flux */
+    int surface_flux;             /* perrk_surface_flux */
+} perrk_scheme_desc;
+
+typedef struct {
+    int precision;                /* perrk_precision: FP64, or FP32 fluxes with float64 state/relaxation */
+    int relaxation;               /* 1: P-ERRK (relaxed), 0: plain P-ERK (gamma = 1) */
+    int newton_max_it;            /* maximum Newton passes per step (>= 0) */
+    double newton_tol_r;          /* stop when |r| <= tol_r * sum omega J |s(U_n)| */
+    double newton_tol_g;          /* stop when |gamma update| <= tol_g */
+    int guess;                    /* perrk_guess: initial Newton guess */
+    int target;                   /* perrk_target: which entropy equality is enforced */
+    int use_graph;                /* 1: capture one step in a CUDA graph and replay it */
+} perrk_options;
+
+/* Per-step record (perrk_step fills one per step when info != NULL). */
+typedef struct {
+    double gamma;                 /* relaxation parameter taken */
+    double H_n;                   /* H(U_n) */
+    double dH;                    /* Delta H (eq. EntropyChangeDefinition) */
+    double H_next;                /* H(U_{n+1}) */
+    double t;                     /* time after the step, t_n + gamma dt */
+    double gamma_guess;           /* initial Newton guess used */
+    int32_t newton_iters;         /* full-state Newton passes */
+    uint32_t flags;               /* PERRK_FLAG_* */
+} perrk_step_info;
+
+typedef struct perrk_ctx perrk_ctx;
+
+/* Fill opts with defaults: FP64, relaxed, max_it 10, tol_r 1e-14, tol_g 1e-14,
+ * guess PREV (Sec. 3.1: gamma_{n-1}, 1 at the first step), target DELTA_H, no graph. */
+void perrk_default_options(perrk_options *opts);
+
+/* Validate and copy mesh and scheme, compute LGL tables and metric terms,
+ * allocate device storage on the current device.  Returns INVALID_ARG (and
+ * *out = NULL) for: N != 3, bad dims, face rows not pairing '+' with the
+ * matching '-' face, faces whose nodes do not coincide up to a translation,
+ * non-positive Jacobians, partition ids out of range, a1 + asub != c,
+ * E below the order's minimum or above S, b_i != 0 where some member is
+ * inactive, nonzero asub at inactive or first-active rows. */
+perrk_status perrk_create(const perrk_mesh_desc *mesh, const perrk_scheme_desc *scheme,
+                          const perrk_options *opts, perrk_ctx **out);
+
+/* n independent instances advanced together (one launch per stage covers all
+ * instances' active elements; the Newton solves run per instance in one
+ * launch per pass).  Instance k has its own mesh[k], scheme[k] and time step;
+ * all schemes share equation, fluxes and order p.  States are concatenated in
+ * instance order: [V][sum n_elem][NP]. */
+perrk_status perrk_create_batched(int n, const perrk_mesh_desc *mesh, const perrk_scheme_desc *scheme,
+                                  const perrk_options *opts, perrk_ctx **out);
+
+void perrk_destroy(perrk_ctx *ctx);
+
+/* Build a P-ERK family of order p (2, 3, 4) with members E[0..R-1] and
+ * S = max E in the low-storage form above (host only, no GPU needed).
+ * Archetypes of appendix A: p = 2 eq. PERK_ButcherTableauClassic_p2_E36 with
+ * c_i = (i-1)/(2(S-1)); p = 3 eq. PERK_ButcherTableauOwn_p3 with
+ * c_i = (i-1)/(S-3), row S read as (1/2 - a, a) and a_{S,S-1} = (1 - a_{S-1,S-2})/4;
+ * p = 4 eq. PERK_ButcherTableau_p4 with eq. 4thOrderPERK_BaseCoeffs and c_2..c_{S-3} = 1.
+ * The paper's optimised free coefficients are not printed; here p = 2 matches
+ * the Taylor coefficients 1/j! of exp up to degree E, p = 3/4 take
+ * a_{i,i-1} = c_i/8 on free rows and a_{S-1,S-2} = 1/4 (p = 3).
+ * Outputs (caller-allocated): c[S], b[S], a1[R][S], asub[R][S]; *S_out = S. */
+perrk_status perrk_build_tableau(int p, int R, const int32_t *E, int S_cap, int *S_out, double *c, double *b,
+                                 double *a1, double *asub);
+
+/* Total elements, variables, nodes per element and instances of ctx. */
+perrk_status perrk_shape(const perrk_ctx *ctx, int *n_elem, int *nvar, int *np, int *n_inst);
+
+/* Copy a state (SoA, float64, n_elem*NP*V values) in (on_device = 0: host
+ * memory, 1: device memory).  Resets t = 0, gamma_{n-1} = 1 and sets
+ * H_n = H(U_0) = H(u), A_n = sum omega J |s(u)| for every instance. */
+perrk_status perrk_set_state(perrk_ctx *ctx, const double *u, int on_device, void *stream);
+perrk_status perrk_get_state(perrk_ctx *ctx, double *u, int on_device, void *stream);
+
+/* Set the time step of instance inst (-1: all).  Coefficients dt * a are
+ * recomputed; a captured graph is re-instantiated on the next step. */
+perrk_status perrk_set_dt(perrk_ctx *ctx, int inst, double dt);
+
+/* Advance nsteps steps.  info: NULL (asynchronous) or host array of
+ * nsteps * n_inst records (step-major), which forces a stream sync. */
+perrk_status perrk_step(perrk_ctx *ctx, int nsteps, perrk_step_info *info, void *stream);
+
+/* H(U) = sum omega J s(U) of the current state per instance (host array [n_inst]); syncs. */
+perrk_status perrk_entropy(perrk_ctx *ctx, double *H, void *stream);
+
+/* Enqueue exactly one stage kernel (stage index 0..S-1, 0-based) of the
+ * step on the context's current buffers (for timing and profiling; the
+ * result is the stage's K_i).  Asynchronous on stream. */
+perrk_status perrk_launch_stage(perrk_ctx *ctx, int stage, void *stream);
+
+/* Static facts of one stage launch: elements evaluated and the algorithmic
+ * bytes it must move (own-element reads of U_n, K_1, K_{i-1} as the stage
+ * rows require, the K_i write, the d read/write at stages with b_i != 0,
+ * geometry and index data; neighbour face reads are not counted).  Also the
+ * stages per step, the number of kernels one step launches and the DOF-stage
+ * updates (sum_r E^(r) M^(r), eq. RHSEvals) of one step. */
+perrk_status perrk_stage_info(const perrk_ctx *ctx, int stage, int64_t *n_active, int64_t *bytes, int *n_stages,
+                              int *kernels_per_step, int64_t *dof_stage_per_step);
+
+/* One evaluation of F on all elements: u_in, k_out device arrays [V][n_elem][NP]. */
+perrk_status perrk_rhs(perrk_ctx *ctx, const double *u_in, double *k_out, void *stream);
+
+/* Learned Newton guess (spec form 4): a 2x64 tanh MLP on the features of
+ * perrk_mlp_features.  weights: host float32 array of perrk_mlp_size() values
+ * laid out W1[64][F], b1[64], W2[64][64], b2[64], W3[64], b3, then F input
+ * means, F input scales, an output scale; NULL disables it. */
+int perrk_mlp_size(void);
+int perrk_mlp_features(void);
+perrk_status perrk_set_mlp(perrk_ctx *ctx, const float *weights, int n);
+
+/* Train the MLP on the device with the library's own forward/backward/Adam
+ * kernels: feats [n][F], target [n] (host float32), in/out weights as above
+ * (updated in place), epochs of full-batch Adam with learning rate lr.
+ * loss_out (nullable): final mean squared error. */
+perrk_status perrk_mlp_train(const float *feats, const float *target, int n, float *weights,
+                             int epochs, float lr, float *loss_out, void *stream);
+
+/* Full-batch gradient of the mean squared error of the MLP (same layout as
+ * weights; only the network parameters, the normalisation entries are 0):
+ * grad_out host float32 [perrk_mlp_size()], loss_out host float32 (nullable).
+ * Used to check the device backward pass against an independent one. */
+perrk_status perrk_mlp_grad(const float *feats, const float *target, int n, const float *weights, float *grad_out,
+                            float *loss_out, void *stream);
+
+/* Last CUDA error string seen by this thread (static storage). */
+const char *perrk_last_error(void);
+const char *perrk_status_string(perrk_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PERRK_H */

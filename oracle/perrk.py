@@ -14,8 +14,10 @@ Relaxation (eq. RelaxationEquation and its derivative, Sec. 3.1):
 with H_target = H_n + g Delta H (eq. EntropyConservationRRKM_Short), = H_n
 (entropy kept from step to step, Sec. 4.1.1) or = H(U_0) (Sec. 4.1.2).
 Newton-Raphson with unit step from the guess (gamma_{n-1}, 1 at the first
-step); stop on |r| <= tol_r * A_n (A_n = sum omega J |s(U_n)|), on
-|dgamma| <= tol_g or after max_it passes; if it did not stop by one of the
+step); stop on |r| <= tol_r * A_n (A_n = sum omega J |s(U_n)|; the Newton
+correction that pass yields is still applied, which costs no pass and makes
+gamma insensitive to rounding at the threshold), on |dgamma| <= tol_g or
+after max_it passes; if it did not stop by one of the
 two tolerances, or gamma is not in (0.5, 1.5), take gamma = 1 (Sec. 3.2,
 fallback of Sec. 3.2.1).  Relaxed update (eq. RRKM_Update):
 U_{n+1} = U_n + gamma dt d, t_{n+1} = t_n + gamma dt.
@@ -122,6 +124,10 @@ class Solver:
             rp = self.dot_w(Ug, dt * d) - dtgt
             it += 1
             if abs(r) <= o.tol_r * A_n:
+                # residual small enough: no further pass, but the correction
+                # this pass already yields is applied (Sec. 3.1 reading)
+                if np.isfinite(r) and np.isfinite(rp) and rp != 0.0:
+                    g = g - r / rp
                 converged = True
                 break
             if not np.isfinite(r) or not np.isfinite(rp) or rp == 0.0:

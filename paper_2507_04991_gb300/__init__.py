@@ -1,0 +1,401 @@
+"""Python binding of libperrk (the GB300 P-ERRK multirate stage loop).
+
+Argument marshalling only: every computation runs in the CUDA kernels of
+``libperrk.so`` behind the C ABI declared in ``include/perrk.h``.  The
+functions carry the C names.  There is no CPU fallback: if the library is
+missing, ``load()`` raises.
+
+Device arrays are passed as raw pointers (``torch.Tensor.data_ptr()``),
+streams as ``torch.cuda.Stream.cuda_stream`` (0 = legacy default stream).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libperrk.so")
+
+PERRK_OK, PERRK_INVALID_ARG, PERRK_CUDA_ERROR, PERRK_NONPHYSICAL_STATE = 0, 1, 2, 3
+PERRK_TIMEOUT, PERRK_OUT_OF_MEMORY, PERRK_NOT_SUPPORTED = 4, 5, 6
+BURGERS_1D, EULER_1D, EULER_2D, EULER_3D = 0, 1, 2, 3
+VOLUME_EC = 0
+SURFACE_EC, SURFACE_ES_RUSANOV = 0, 1
+FP64, MIXED = 0, 1
+GUESS_ONE, GUESS_PREV, GUESS_MLP = 0, 1, 2
+TARGET_DELTA_H, TARGET_PREV, TARGET_INITIAL = 0, 1, 2
+FLAG_NEWTON_FALLBACK, FLAG_NONPHYSICAL, FLAG_NONFINITE = 1, 2, 4
+
+EXPORTED = [
+    "perrk_default_options", "perrk_create", "perrk_create_batched", "perrk_destroy", "perrk_build_tableau",
+    "perrk_shape", "perrk_set_state", "perrk_get_state", "perrk_set_dt", "perrk_step", "perrk_entropy",
+    "perrk_rhs", "perrk_mlp_size", "perrk_mlp_features", "perrk_set_mlp", "perrk_mlp_train", "perrk_mlp_grad",
+    "perrk_last_error", "perrk_status_string", "perrk_launch_stage", "perrk_stage_info",
+]
+
+
+class perrk_mesh_desc(C.Structure):
+    _fields_ = [("dim", C.c_int), ("N", C.c_int), ("n_elem", C.c_int), ("node_coords", C.c_void_p),
+                ("n_faces", C.c_int), ("faces", C.c_void_p), ("partition_id", C.c_void_p)]
+
+
+class perrk_scheme_desc(C.Structure):
+    _fields_ = [("order", C.c_int), ("S", C.c_int), ("R", C.c_int), ("E", C.c_void_p), ("c", C.c_void_p),
+                ("b", C.c_void_p), ("a1", C.c_void_p), ("asub", C.c_void_p), ("equation", C.c_int),
+                ("gamma_gas", C.c_double), ("volume_flux", C.c_int), ("surface_flux", C.c_int)]
+
+
+class perrk_options(C.Structure):
+    _fields_ = [("precision", C.c_int), ("relaxation", C.c_int), ("newton_max_it", C.c_int),
+                ("newton_tol_r", C.c_double), ("newton_tol_g", C.c_double), ("guess", C.c_int),
+                ("target", C.c_int), ("use_graph", C.c_int)]
+
+
+class perrk_step_info(C.Structure):
+    _fields_ = [("gamma", C.c_double), ("H_n", C.c_double), ("dH", C.c_double), ("H_next", C.c_double),
+                ("t", C.c_double), ("gamma_guess", C.c_double), ("newton_iters", C.c_int32),
+                ("flags", C.c_uint32)]
+
+
+class PerrkError(RuntimeError):
+    def __init__(self, status, what):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)} ({last_error()})")
+
+
+_lib = None
+
+
+def load(path=LIB_PATH):
+    """Load libperrk.so (build it first with ``__graft_entry__.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libperrk.so not built ({path}); run __graft_entry__.build()")
+    lib = C.CDLL(path)
+    P, I, D, V = C.c_void_p, C.c_int, C.c_double, None
+    sig = {
+        "perrk_default_options": (V, [P]),
+        "perrk_create": (I, [P, P, P, P]),
+        "perrk_create_batched": (I, [I, P, P, P, P]),
+        "perrk_destroy": (V, [P]),
+        "perrk_build_tableau": (I, [I, I, P, I, P, P, P, P, P]),
+        "perrk_shape": (I, [P, P, P, P, P]),
+        "perrk_set_state": (I, [P, P, I, P]),
+        "perrk_get_state": (I, [P, P, I, P]),
+        "perrk_set_dt": (I, [P, I, D]),
+        "perrk_step": (I, [P, I, P, P]),
+        "perrk_entropy": (I, [P, P, P]),
+        "perrk_rhs": (I, [P, P, P, P]),
+        "perrk_mlp_size": (I, []),
+        "perrk_mlp_features": (I, []),
+        "perrk_set_mlp": (I, [P, P, I]),
+        "perrk_mlp_train": (I, [P, P, I, P, I, C.c_float, P, P]),
+        "perrk_mlp_grad": (I, [P, P, I, P, P, P, P]),
+        "perrk_last_error": (C.c_char_p, []),
+        "perrk_launch_stage": (I, [P, I, P]),
+        "perrk_stage_info": (I, [P, I, P, P, P, P, P]),
+        "perrk_status_string": (C.c_char_p, [I]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def last_error():
+    return load().perrk_last_error().decode()
+
+
+def status_string(s):
+    return load().perrk_status_string(int(s)).decode()
+
+
+def _check(status, what):
+    if status != PERRK_OK:
+        raise PerrkError(status, what)
+
+
+def _ptr(a):
+    return C.c_void_p(a.ctypes.data) if a is not None else None
+
+
+# ------------------------------------------------------------ C-named calls
+
+def perrk_default_options():
+    o = perrk_options()
+    load().perrk_default_options(C.byref(o))
+    return o
+
+
+def perrk_build_tableau(p, E):
+    E = np.ascontiguousarray(E, dtype=np.int32)
+    S = int(E.max())
+    R = len(E)
+    c = np.zeros(S)
+    b = np.zeros(S)
+    a1 = np.zeros((R, S))
+    asub = np.zeros((R, S))
+    S_out = C.c_int(0)
+    _check(load().perrk_build_tableau(int(p), R, _ptr(E), S, C.byref(S_out), _ptr(c), _ptr(b), _ptr(a1), _ptr(asub)),
+           "perrk_build_tableau")
+    return c, b, a1, asub
+
+
+class _Keep:
+    """Host arrays referenced by a descriptor (kept alive for the call)."""
+
+    def __init__(self):
+        self.arrays = []
+
+    def add(self, a):
+        self.arrays.append(a)
+        return _ptr(a)
+
+
+def mesh_desc(coords, faces, part, keep):
+    coords = np.ascontiguousarray(coords, dtype=np.float64)
+    faces = np.ascontiguousarray(faces, dtype=np.int32)
+    part = np.ascontiguousarray(part, dtype=np.int32)
+    m = perrk_mesh_desc()
+    m.dim = coords.shape[2]
+    m.N = 3
+    m.n_elem = coords.shape[0]
+    m.node_coords = keep.add(coords)
+    m.n_faces = faces.shape[0]
+    m.faces = keep.add(faces)
+    m.partition_id = keep.add(part)
+    return m
+
+
+def scheme_desc(order, E, c, b, a1, asub, equation, surface_flux, gamma_gas, keep):
+    E = np.ascontiguousarray(E, dtype=np.int32)
+    s = perrk_scheme_desc()
+    s.order = int(order)
+    s.S = len(c)
+    s.R = len(E)
+    s.E = keep.add(E)
+    s.c = keep.add(np.ascontiguousarray(c, dtype=np.float64))
+    s.b = keep.add(np.ascontiguousarray(b, dtype=np.float64))
+    s.a1 = keep.add(np.ascontiguousarray(a1, dtype=np.float64))
+    s.asub = keep.add(np.ascontiguousarray(asub, dtype=np.float64))
+    s.equation = int(equation)
+    s.gamma_gas = float(gamma_gas)
+    s.volume_flux = VOLUME_EC
+    s.surface_flux = int(surface_flux)
+    return s
+
+
+def perrk_create_batched(meshes, schemes, opts):
+    n = len(meshes)
+    marr = (perrk_mesh_desc * n)(*meshes)
+    sarr = (perrk_scheme_desc * n)(*schemes)
+    h = C.c_void_p()
+    _check(load().perrk_create_batched(n, marr, sarr, C.byref(opts), C.byref(h)), "perrk_create_batched")
+    return h
+
+
+def perrk_create(mesh, scheme, opts):
+    h = C.c_void_p()
+    _check(load().perrk_create(C.byref(mesh), C.byref(scheme), C.byref(opts), C.byref(h)), "perrk_create")
+    return h
+
+
+def perrk_destroy(h):
+    if h:
+        load().perrk_destroy(h)
+
+
+def perrk_shape(h):
+    v = [C.c_int() for _ in range(4)]
+    _check(load().perrk_shape(h, *[C.byref(x) for x in v]), "perrk_shape")
+    return tuple(x.value for x in v)
+
+
+def perrk_set_state(h, u, on_device=False, stream=0):
+    """u: host float64 ndarray, or a raw pointer (int) to device memory
+    (on_device) or to host memory (e.g. pinned)."""
+    if isinstance(u, int):
+        ptr, keep = C.c_void_p(u), None
+    else:
+        keep = np.ascontiguousarray(u, dtype=np.float64)
+        ptr = _ptr(keep)
+    _check(load().perrk_set_state(h, ptr, int(bool(on_device)), C.c_void_p(stream)), "perrk_set_state")
+    del keep
+
+
+def perrk_get_state(h, out=None, on_device=False, stream=0):
+    """out: host ndarray (allocated when None), or a raw pointer (int) to
+    device memory (on_device) or to host memory."""
+    if isinstance(out, int):
+        _check(load().perrk_get_state(h, C.c_void_p(out), int(bool(on_device)), C.c_void_p(stream)), "perrk_get_state")
+        return out
+    n_elem, nvar, npn, _ = perrk_shape(h)
+    if out is None:
+        out = np.empty((nvar, n_elem, npn))
+    _check(load().perrk_get_state(h, _ptr(out), 0, C.c_void_p(stream)), "perrk_get_state")
+    return out
+
+
+def perrk_set_dt(h, dt, inst=-1):
+    _check(load().perrk_set_dt(h, int(inst), float(dt)), "perrk_set_dt")
+
+
+def perrk_step(h, nsteps, info=True, stream=0):
+    """Advance nsteps; returns a list (per step) of lists (per instance) of dicts when info."""
+    if not info:
+        _check(load().perrk_step(h, int(nsteps), None, C.c_void_p(stream)), "perrk_step")
+        return None
+    n_inst = perrk_shape(h)[3]
+    recs = (perrk_step_info * (nsteps * n_inst))()
+    _check(load().perrk_step(h, int(nsteps), recs, C.c_void_p(stream)), "perrk_step")
+    out = []
+    for k in range(nsteps):
+        row = []
+        for i in range(n_inst):
+            r = recs[k * n_inst + i]
+            row.append(dict(gamma=r.gamma, H_n=r.H_n, dH=r.dH, H_next=r.H_next, t=r.t, gamma_guess=r.gamma_guess,
+                            iters=r.newton_iters, flags=r.flags))
+        out.append(row)
+    return out
+
+
+def perrk_entropy(h, stream=0):
+    n_inst = perrk_shape(h)[3]
+    H = np.zeros(n_inst)
+    _check(load().perrk_entropy(h, _ptr(H), C.c_void_p(stream)), "perrk_entropy")
+    return H
+
+
+def perrk_rhs(h, u_ptr, k_ptr, stream=0):
+    _check(load().perrk_rhs(h, C.c_void_p(u_ptr), C.c_void_p(k_ptr), C.c_void_p(stream)), "perrk_rhs")
+
+
+def perrk_launch_stage(h, stage, stream=0):
+    _check(load().perrk_launch_stage(h, int(stage), C.c_void_p(stream)), "perrk_launch_stage")
+
+
+def perrk_stage_info(h, stage):
+    na, by, ns, kps, dsp = C.c_int64(), C.c_int64(), C.c_int(), C.c_int(), C.c_int64()
+    _check(load().perrk_stage_info(h, int(stage), C.byref(na), C.byref(by), C.byref(ns), C.byref(kps), C.byref(dsp)),
+           "perrk_stage_info")
+    return dict(n_active=na.value, bytes=by.value, n_stages=ns.value, kernels_per_step=kps.value,
+                dof_stage_per_step=dsp.value)
+
+
+def perrk_mlp_size():
+    return load().perrk_mlp_size()
+
+
+def perrk_mlp_features():
+    return load().perrk_mlp_features()
+
+
+def perrk_set_mlp(h, weights):
+    if weights is None:
+        _check(load().perrk_set_mlp(h, None, 0), "perrk_set_mlp")
+        return
+    w = np.ascontiguousarray(weights, dtype=np.float32)
+    _check(load().perrk_set_mlp(h, _ptr(w), w.size), "perrk_set_mlp")
+
+
+def perrk_mlp_train(feats, target, weights, epochs, lr, stream=0):
+    X = np.ascontiguousarray(feats, dtype=np.float32)
+    T = np.ascontiguousarray(target, dtype=np.float32)
+    W = np.ascontiguousarray(weights, dtype=np.float32).copy()
+    loss = C.c_float(0.0)
+    _check(load().perrk_mlp_train(_ptr(X), _ptr(T), len(T), _ptr(W), int(epochs), C.c_float(lr), C.byref(loss),
+                                  C.c_void_p(stream)), "perrk_mlp_train")
+    return W, loss.value
+
+
+def perrk_mlp_grad(feats, target, weights, stream=0):
+    X = np.ascontiguousarray(feats, dtype=np.float32)
+    T = np.ascontiguousarray(target, dtype=np.float32)
+    W = np.ascontiguousarray(weights, dtype=np.float32)
+    G = np.zeros(perrk_mlp_size(), dtype=np.float32)
+    loss = C.c_float(0.0)
+    _check(load().perrk_mlp_grad(_ptr(X), _ptr(T), len(T), _ptr(W), _ptr(G), C.byref(loss), C.c_void_p(stream)),
+           "perrk_mlp_grad")
+    return G, loss.value
+
+
+# ------------------------------------------------------------ convenience
+
+EQUATION_CODES = {"burgers1d": BURGERS_1D, "euler1d": EULER_1D, "euler2d": EULER_2D, "euler3d": EULER_3D}
+SURFACE_CODES = {"ec": SURFACE_EC, "es": SURFACE_ES_RUSANOV, "es_rusanov": SURFACE_ES_RUSANOV}
+
+
+def options(precision=FP64, relaxation=True, max_it=10, tol_r=1e-14, tol_g=1e-14, guess=GUESS_PREV,
+            target=TARGET_DELTA_H, use_graph=False):
+    o = perrk_default_options()
+    o.precision = precision
+    o.relaxation = int(bool(relaxation))
+    o.newton_max_it = max_it
+    o.newton_tol_r = tol_r
+    o.newton_tol_g = tol_g
+    o.guess = guess
+    o.target = target
+    o.use_graph = int(bool(use_graph))
+    return o
+
+
+class Solver:
+    """One context over one mesh or a batch of meshes.  Each problem is any
+    object with fields coords, faces, part, E, order, equation, surface_flux,
+    gamma_gas (and optionally dt, u0)."""
+
+    def __init__(self, problems, opts=None, tableaux=None):
+        if not isinstance(problems, (list, tuple)):
+            problems = [problems]
+        self.problems = problems
+        self.keep = _Keep()
+        meshes, schemes = [], []
+        for k, pb in enumerate(problems):
+            meshes.append(mesh_desc(pb.coords, pb.faces, pb.part, self.keep))
+            tab = tableaux[k] if tableaux else perrk_build_tableau(pb.order, pb.E)
+            schemes.append(scheme_desc(pb.order, pb.E, *tab, EQUATION_CODES[pb.equation],
+                                       SURFACE_CODES[pb.surface_flux], pb.gamma_gas, self.keep))
+        self.opts = opts or options()
+        self.h = perrk_create_batched(meshes, schemes, self.opts)
+        self.n_elem, self.nvar, self.np, self.n_inst = perrk_shape(self.h)
+        for k, pb in enumerate(problems):
+            if getattr(pb, "dt", None):
+                perrk_set_dt(self.h, pb.dt, k)
+        if all(getattr(pb, "u0", None) is not None for pb in problems):
+            u0 = np.concatenate([np.asarray(pb.u0) for pb in problems], axis=1)
+            perrk_set_state(self.h, u0)
+
+    def close(self):
+        if self.h:
+            perrk_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_state(self, u, on_device=False, stream=0):
+        perrk_set_state(self.h, u, on_device, stream)
+
+    def state(self):
+        return perrk_get_state(self.h)
+
+    def step(self, nsteps=1, info=True, stream=0):
+        return perrk_step(self.h, nsteps, info, stream)
+
+    def set_dt(self, dt, inst=-1):
+        perrk_set_dt(self.h, dt, inst)
+
+    def entropy(self):
+        return perrk_entropy(self.h)
+
+    def set_mlp(self, w):
+        perrk_set_mlp(self.h, w)

@@ -1,0 +1,425 @@
+// C ABI of libperrk: context lifetime, state transfer, the P-ERRK step
+// sequence and its CUDA-graph capture.  One step is
+//   S stage launches (stage i over its active element prefix)
+//   -> relax_init (Delta H, Newton guess) [-> MLP guess]
+//   -> newton_max_it Newton passes (each returns at once when the solve is done)
+//   -> update (U_{n+1} = U_n + gamma dt d, t += gamma dt, step record).
+// Nothing in a step depends on host control flow, so the whole step is one
+// capturable launch sequence.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "perrk_internal.h"
+
+struct perrk_ctx {
+    perrk::Ctx c;
+    cudaStream_t capture_stream = nullptr;
+    long long host_steps = 0;  // steps since the last set_state (mirrors the device counter)
+};
+
+namespace perrk {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string &e) { g_err = e; }
+
+perrk_status cuda_check(int err, const char *what) {
+    if (err == (int)cudaSuccess) return PERRK_OK;
+    char buf[256];
+    snprintf(buf, sizeof buf, "%s: %s", what, cudaGetErrorString((cudaError_t)err));
+    g_err = buf;
+    return err == (int)cudaErrorMemoryAllocation ? PERRK_OUT_OF_MEMORY : PERRK_CUDA_ERROR;
+}
+
+#define PERRK_TRY(x)                          \
+    do {                                      \
+        perrk_status _s = (x);                \
+        if (_s != PERRK_OK) return _s;        \
+    } while (0)
+#define PERRK_CUDA(x, what) PERRK_TRY(cuda_check((int)(x), what))
+
+template <typename T>
+static perrk_status upload(T *&dst, const std::vector<T> &src, const char *what) {
+    if (src.empty()) {
+        dst = nullptr;
+        return PERRK_OK;
+    }
+    PERRK_CUDA(cudaMalloc((void **)&dst, src.size() * sizeof(T)), what);
+    PERRK_CUDA(cudaMemcpy(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice), what);
+    return PERRK_OK;
+}
+
+static void free_ctx(Ctx &c) {
+    void *ptrs[] = {c.U, c.K1, c.Ka, c.Kb, c.d, c.e_dh, c.g_node, c.g_elem, c.g_fnorm, c.g_wJ, c.g_nbr, c.g_gp,
+                    c.g_elist, c.g_chunk_inst, c.g_chunk_e0, c.g_chunk_e1, c.g_inst_chunk0, c.g_inst_nchunks,
+                    c.g_coef, c.g_coef_f, c.g_scal, c.g_partials, c.g_counters, c.g_flags, c.g_records, c.g_mlp};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (c.graph_exec) cudaGraphExecDestroy((cudaGraphExec_t)c.graph_exec);
+    if (c.graph) cudaGraphDestroy((cudaGraph_t)c.graph);
+    c.graph_exec = c.graph = nullptr;
+}
+
+static perrk_status upload_coefficients(Ctx &c) {
+    std::vector<StageCoef> coef;
+    std::vector<StageCoefF> coef_f;
+    stage_coefficients(c, coef, coef_f);
+    PERRK_CUDA(cudaMemcpy(c.g_coef, coef.data(), coef.size() * sizeof(StageCoef), cudaMemcpyHostToDevice), "coef upload");
+    PERRK_CUDA(cudaMemcpy(c.g_coef_f, coef_f.data(), coef_f.size() * sizeof(StageCoefF), cudaMemcpyHostToDevice),
+               "coef upload");
+    for (int k = 0; k < c.n_inst; ++k)
+        PERRK_CUDA(cudaMemcpy(&c.g_scal[k].dt, &c.inst[k].dt, sizeof(double), cudaMemcpyHostToDevice), "dt upload");
+    c.graph_dirty = true;
+    return PERRK_OK;
+}
+
+static perrk_status alloc_ctx(Ctx &c) {
+    const size_t nstate = (size_t)c.V * c.n_elem * c.NP;
+    double **bufs[] = {&c.U, &c.K1, &c.Ka, &c.Kb, &c.d};
+    for (double **b : bufs) {
+        PERRK_CUDA(cudaMalloc((void **)b, nstate * sizeof(double)), "state alloc");
+        PERRK_CUDA(cudaMemset(*b, 0, nstate * sizeof(double)), "state clear");
+    }
+    PERRK_CUDA(cudaMalloc((void **)&c.e_dh, (size_t)c.n_elem * sizeof(double)), "e_dh alloc");
+    PERRK_CUDA(cudaMemset(c.e_dh, 0, (size_t)c.n_elem * sizeof(double)), "e_dh clear");
+    PERRK_TRY(upload(c.g_node, c.geo_node, "geometry"));
+    PERRK_TRY(upload(c.g_elem, c.geo_elem, "geometry"));
+    PERRK_TRY(upload(c.g_fnorm, c.fnorm, "normals"));
+    PERRK_TRY(upload(c.g_wJ, c.wJ, "weights"));
+    PERRK_TRY(upload(c.g_nbr, c.nbr, "neighbours"));
+    PERRK_TRY(upload(c.g_gp, c.gp_of_elem, "partitions"));
+    PERRK_TRY(upload(c.g_elist, c.elist, "element list"));
+    PERRK_TRY(upload(c.g_chunk_inst, c.chunk_inst, "chunks"));
+    PERRK_TRY(upload(c.g_chunk_e0, c.chunk_e0, "chunks"));
+    PERRK_TRY(upload(c.g_chunk_e1, c.chunk_e1, "chunks"));
+    std::vector<int32_t> ic0(c.n_inst), inc(c.n_inst);
+    for (int k = 0; k < c.n_inst; ++k) {
+        ic0[k] = c.inst[k].chunk0;
+        inc[k] = c.inst[k].n_chunks;
+    }
+    PERRK_TRY(upload(c.g_inst_chunk0, ic0, "chunks"));
+    PERRK_TRY(upload(c.g_inst_nchunks, inc, "chunks"));
+    PERRK_CUDA(cudaMalloc((void **)&c.g_coef, (size_t)c.S * c.n_gp * sizeof(StageCoef)), "coef alloc");
+    PERRK_CUDA(cudaMalloc((void **)&c.g_coef_f, (size_t)c.S * c.n_gp * sizeof(StageCoefF)), "coef alloc");
+    std::vector<InstScalars> scal(c.n_inst);
+    for (auto &s : scal) {
+        memset(&s, 0, sizeof s);
+        s.gamma = 1.0;
+        for (int k = 0; k < 3; ++k) s.hist_gamma[k] = 1.0;
+    }
+    PERRK_TRY(upload(c.g_scal, scal, "scalars"));
+    PERRK_CUDA(cudaMalloc((void **)&c.g_partials, c.chunk_inst.size() * 8 * sizeof(double)), "partials alloc");
+    PERRK_CUDA(cudaMalloc((void **)&c.g_counters, (size_t)c.n_inst * sizeof(uint32_t)), "counters alloc");
+    PERRK_CUDA(cudaMemset(c.g_counters, 0, (size_t)c.n_inst * sizeof(uint32_t)), "counters clear");
+    PERRK_CUDA(cudaMalloc((void **)&c.g_flags, sizeof(uint32_t)), "flags alloc");
+    PERRK_CUDA(cudaMemset(c.g_flags, 0, sizeof(uint32_t)), "flags clear");
+    c.rec_cap = 256;
+    PERRK_CUDA(cudaMalloc((void **)&c.g_records, (size_t)c.rec_cap * c.n_inst * sizeof(perrk_step_info)), "records");
+    return upload_coefficients(c);
+}
+
+static perrk_status enqueue_step(Ctx &c, cudaStream_t st) {
+    for (int i = 0; i < c.S; ++i) {
+        double *Kout = (i == 0) ? c.K1 : ((i % 2) ? c.Ka : c.Kb);
+        const double *Kprev = (i <= 1) ? c.K1 : (((i - 1) % 2) ? c.Ka : c.Kb);
+        PERRK_TRY(launch_stage(c, i, c.U, Kout, Kprev, false, st));
+    }
+    PERRK_TRY(launch_relax_init(c, st));
+    if (c.opt.relaxation) {
+        if (c.opt.guess == PERRK_GUESS_MLP && c.mlp_on) PERRK_TRY(launch_mlp_guess(c, st));
+        for (int it = 0; it < c.opt.newton_max_it; ++it) PERRK_TRY(launch_newton_pass(c, st));
+    }
+    return launch_update(c, 0, st);
+}
+
+}  // namespace perrk
+
+using namespace perrk;
+
+extern "C" {
+
+void perrk_default_options(perrk_options *o) {
+    if (!o) return;
+    o->precision = PERRK_FP64;
+    o->relaxation = 1;
+    o->newton_max_it = 10;
+    o->newton_tol_r = 1e-14;
+    o->newton_tol_g = 1e-14;
+    o->guess = PERRK_GUESS_PREV;
+    o->target = PERRK_TARGET_DELTA_H;
+    o->use_graph = 0;
+}
+
+perrk_status perrk_create_batched(int n, const perrk_mesh_desc *mesh, const perrk_scheme_desc *scheme,
+                                  const perrk_options *opts, perrk_ctx **out) {
+    if (!out) {
+        set_error("out is NULL");
+        return PERRK_INVALID_ARG;
+    }
+    *out = nullptr;
+    perrk_ctx *h = new (std::nothrow) perrk_ctx();
+    if (!h) return PERRK_OUT_OF_MEMORY;
+    std::string err;
+    perrk_status st = build_ctx(h->c, n, mesh, scheme, opts, err);
+    if (st != PERRK_OK) {
+        set_error(err);
+        delete h;
+        return st;
+    }
+    st = alloc_ctx(h->c);
+    if (st == PERRK_OK) st = cuda_check((int)cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking), "stream");
+    if (st != PERRK_OK) {
+        free_ctx(h->c);
+        delete h;
+        return st;
+    }
+    *out = h;
+    return PERRK_OK;
+}
+
+perrk_status perrk_create(const perrk_mesh_desc *mesh, const perrk_scheme_desc *scheme, const perrk_options *opts,
+                          perrk_ctx **out) {
+    return perrk_create_batched(1, mesh, scheme, opts, out);
+}
+
+void perrk_destroy(perrk_ctx *h) {
+    if (!h) return;
+    cudaDeviceSynchronize();
+    free_ctx(h->c);
+    if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
+    delete h;
+}
+
+perrk_status perrk_shape(const perrk_ctx *h, int *n_elem, int *nvar, int *np, int *n_inst) {
+    if (!h) return PERRK_INVALID_ARG;
+    if (n_elem) *n_elem = h->c.n_elem;
+    if (nvar) *nvar = h->c.V;
+    if (np) *np = h->c.NP;
+    if (n_inst) *n_inst = h->c.n_inst;
+    return PERRK_OK;
+}
+
+perrk_status perrk_set_state(perrk_ctx *h, const double *u, int on_device, void *stream) {
+    if (!h || !u) return PERRK_INVALID_ARG;
+    Ctx &c = h->c;
+    const size_t bytes = (size_t)c.V * c.n_elem * c.NP * sizeof(double);
+    cudaStream_t st = (cudaStream_t)stream;
+    PERRK_CUDA(cudaMemcpyAsync(c.U, u, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st),
+               "set_state copy");
+    PERRK_CUDA(cudaMemsetAsync(c.g_flags, 0, sizeof(uint32_t), st), "flags clear");
+    PERRK_TRY(launch_entropy_set(c, st));
+    h->host_steps = 0;
+    if (!on_device) PERRK_CUDA(cudaStreamSynchronize(st), "set_state sync");
+    return PERRK_OK;
+}
+
+perrk_status perrk_get_state(perrk_ctx *h, double *u, int on_device, void *stream) {
+    if (!h || !u) return PERRK_INVALID_ARG;
+    Ctx &c = h->c;
+    const size_t bytes = (size_t)c.V * c.n_elem * c.NP * sizeof(double);
+    cudaStream_t st = (cudaStream_t)stream;
+    PERRK_CUDA(cudaMemcpyAsync(u, c.U, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st),
+               "get_state copy");
+    if (!on_device) PERRK_CUDA(cudaStreamSynchronize(st), "get_state sync");
+    return PERRK_OK;
+}
+
+perrk_status perrk_set_dt(perrk_ctx *h, int inst, double dt) {
+    if (!h || !(dt > 0.0) || !std::isfinite(dt) || inst < -1 || inst >= h->c.n_inst) {
+        set_error("bad instance or dt");
+        return PERRK_INVALID_ARG;
+    }
+    Ctx &c = h->c;
+    PERRK_CUDA(cudaDeviceSynchronize(), "set_dt sync");
+    for (int k = 0; k < c.n_inst; ++k)
+        if (inst < 0 || inst == k) c.inst[k].dt = dt;
+    return upload_coefficients(c);
+}
+
+perrk_status perrk_step(perrk_ctx *h, int nsteps, perrk_step_info *info, void *stream) {
+    if (!h || nsteps < 0) return PERRK_INVALID_ARG;
+    Ctx &c = h->c;
+    for (const Instance &I : c.inst)
+        if (!(I.dt > 0.0)) {
+            set_error("dt not set (perrk_set_dt)");
+            return PERRK_INVALID_ARG;
+        }
+    cudaStream_t st = (cudaStream_t)stream;
+    PERRK_CUDA(cudaMemsetAsync(c.g_flags, 0, sizeof(uint32_t), st), "flags clear");
+    if (c.opt.use_graph && c.graph_dirty) {
+        if (c.graph_exec) cudaGraphExecDestroy((cudaGraphExec_t)c.graph_exec);
+        if (c.graph) cudaGraphDestroy((cudaGraph_t)c.graph);
+        c.graph_exec = c.graph = nullptr;
+        PERRK_CUDA(cudaStreamSynchronize(st), "pre-capture sync");
+        PERRK_CUDA(cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal), "capture begin");
+        perrk_status s = enqueue_step(c, h->capture_stream);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(h->capture_stream, &g);
+        if (s != PERRK_OK) return s;
+        PERRK_CUDA(e, "capture end");
+        cudaGraphExec_t ex = nullptr;
+        PERRK_CUDA(cudaGraphInstantiate(&ex, g, 0), "graph instantiate");
+        c.graph = g;
+        c.graph_exec = ex;
+        c.graph_dirty = false;
+    }
+    long long done = 0;
+    while (done < nsteps) {
+        const long long batch = info ? std::min<long long>(nsteps - done, c.rec_cap) : (nsteps - done);
+        const long long first_slot = h->host_steps % c.rec_cap;
+        for (long long k = 0; k < batch; ++k) {
+            if (c.opt.use_graph) PERRK_CUDA(cudaGraphLaunch((cudaGraphExec_t)c.graph_exec, st), "graph launch");
+            else PERRK_TRY(enqueue_step(c, st));
+            h->host_steps++;
+        }
+        if (info) {
+            std::vector<perrk_step_info> recs((size_t)c.rec_cap * c.n_inst);
+            PERRK_CUDA(cudaMemcpyAsync(recs.data(), c.g_records, recs.size() * sizeof(perrk_step_info),
+                                       cudaMemcpyDeviceToHost, st),
+                       "records copy");
+            PERRK_CUDA(cudaStreamSynchronize(st), "step sync");
+            for (long long k = 0; k < batch; ++k) {
+                long long slot = (first_slot + k) % c.rec_cap;
+                memcpy(info + (size_t)(done + k) * c.n_inst, recs.data() + (size_t)slot * c.n_inst,
+                       (size_t)c.n_inst * sizeof(perrk_step_info));
+            }
+        }
+        done += batch;
+    }
+    if (info) {
+        uint32_t fl = 0;
+        PERRK_CUDA(cudaMemcpy(&fl, c.g_flags, sizeof fl, cudaMemcpyDeviceToHost), "flags read");
+        if (fl & (PERRK_FLAG_NONPHYSICAL | PERRK_FLAG_NONFINITE)) {
+            set_error("non-physical or non-finite state met during the step");
+            return PERRK_NONPHYSICAL_STATE;
+        }
+    }
+    return PERRK_OK;
+}
+
+perrk_status perrk_entropy(perrk_ctx *h, double *H, void *stream) {
+    if (!h || !H) return PERRK_INVALID_ARG;
+    Ctx &c = h->c;
+    cudaStream_t st = (cudaStream_t)stream;
+    PERRK_TRY(launch_entropy(c, 1, st));
+    std::vector<InstScalars> scal(c.n_inst);
+    PERRK_CUDA(cudaMemcpyAsync(scal.data(), c.g_scal, scal.size() * sizeof(InstScalars), cudaMemcpyDeviceToHost, st),
+               "scalars copy");
+    PERRK_CUDA(cudaStreamSynchronize(st), "entropy sync");
+    for (int k = 0; k < c.n_inst; ++k) H[k] = scal[k].H_next;
+    return PERRK_OK;
+}
+
+perrk_status perrk_launch_stage(perrk_ctx *h, int stage, void *stream) {
+    if (!h || stage < 0 || stage >= h->c.S) return PERRK_INVALID_ARG;
+    Ctx &c = h->c;
+    double *Kout = (stage == 0) ? c.K1 : ((stage % 2) ? c.Ka : c.Kb);
+    const double *Kprev = (stage <= 1) ? c.K1 : (((stage - 1) % 2) ? c.Ka : c.Kb);
+    return launch_stage(c, stage, c.U, Kout, Kprev, false, stream);
+}
+
+perrk_status perrk_stage_info(const perrk_ctx *h, int stage, int64_t *n_active, int64_t *bytes, int *n_stages,
+                              int *kernels_per_step, int64_t *dof_stage_per_step) {
+    if (!h || stage < 0 || stage >= h->c.S) return PERRK_INVALID_ARG;
+    const Ctx &c = h->c;
+    const int NF = 2 * c.dim, NFP = ipow4(c.dim - 1);
+    const int64_t per_arr = (int64_t)c.V * c.NP * 8;  // one float64 state array, one element
+    std::vector<StageCoef> coef;
+    std::vector<StageCoefF> coef_f;
+    stage_coefficients(c, coef, coef_f);
+    int64_t tot = 0;
+    const int na = c.n_active[stage];
+    for (int k = 0; k < na; ++k) {
+        const int e = c.elist[k];
+        const StageCoef &sc = coef[(size_t)stage * c.n_gp + c.gp_of_elem[e]];
+        int64_t arrays = 1 /*U*/ + 1 /*K out*/;
+        if (stage > 0) arrays += 1;               // K_1
+        if (stage > 0 && sc.asub != 0.0) arrays += 1;  // K_{i-1}
+        if (sc.b != 0.0) arrays += (sc.first_b != 0.0) ? 1 : 2;  // d write (and read)
+        int64_t geo = c.curved ? (int64_t)c.NP * 5 * 8 + (int64_t)NF * NFP * 2 * 8 : (int64_t)(c.dim + 1 + NF) * 8;
+        if (sc.b != 0.0) geo += (int64_t)c.NP * 8 + 8;  // omega J and the element's Delta H slot
+        tot += arrays * per_arr + geo + 4 * (2 + NF);  // element list, partition id, neighbours
+    }
+    if (n_active) *n_active = na;
+    if (bytes) *bytes = tot;
+    if (n_stages) *n_stages = c.S;
+    if (kernels_per_step) {
+        int k = 0;
+        for (int i = 0; i < c.S; ++i) k += c.n_active[i] > 0 ? 1 : 0;
+        k += 2;  // relax_init + update
+        if (c.opt.relaxation) k += c.opt.newton_max_it + ((c.opt.guess == PERRK_GUESS_MLP && c.mlp_on) ? 1 : 0);
+        *kernels_per_step = k;
+    }
+    if (dof_stage_per_step) {
+        int64_t s = 0;
+        for (int i = 0; i < c.S; ++i) s += (int64_t)c.n_active[i];
+        // stage 1 counts once per element for every member (it is one of the E evaluations)
+        *dof_stage_per_step = s * c.V * c.NP;
+    }
+    return PERRK_OK;
+}
+
+perrk_status perrk_rhs(perrk_ctx *h, const double *u_in, double *k_out, void *stream) {
+    if (!h || !u_in || !k_out) return PERRK_INVALID_ARG;
+    return launch_stage(h->c, 0, u_in, k_out, nullptr, true, stream);
+}
+
+int perrk_mlp_size(void) {
+    const int F = kMlpFeatures, H = kMlpHidden;
+    return H * F + H + H * H + H + H + 1 + 2 * F + 1;
+}
+
+int perrk_mlp_features(void) { return kMlpFeatures; }
+
+perrk_status perrk_set_mlp(perrk_ctx *h, const float *w, int n) {
+    if (!h) return PERRK_INVALID_ARG;
+    Ctx &c = h->c;
+    if (!w) {
+        c.mlp_on = 0;
+        c.graph_dirty = true;
+        return PERRK_OK;
+    }
+    if (n != perrk_mlp_size()) {
+        set_error("MLP weight count mismatch");
+        return PERRK_INVALID_ARG;
+    }
+    if (!c.g_mlp) PERRK_CUDA(cudaMalloc((void **)&c.g_mlp, n * sizeof(float)), "mlp alloc");
+    PERRK_CUDA(cudaMemcpy(c.g_mlp, w, n * sizeof(float), cudaMemcpyHostToDevice), "mlp upload");
+    c.mlp_on = 1;
+    c.graph_dirty = true;
+    return PERRK_OK;
+}
+
+perrk_status perrk_mlp_train(const float *feats, const float *target, int n, float *weights, int epochs, float lr,
+                             float *loss_out, void *stream) {
+    if (!feats || !target || !weights || n <= 0 || epochs < 0) return PERRK_INVALID_ARG;
+    return mlp_train_device(feats, target, n, weights, epochs, lr, loss_out, nullptr, stream);
+}
+
+perrk_status perrk_mlp_grad(const float *feats, const float *target, int n, const float *weights, float *grad_out,
+                            float *loss_out, void *stream) {
+    if (!feats || !target || !weights || !grad_out || n <= 0) return PERRK_INVALID_ARG;
+    std::vector<float> w(weights, weights + perrk_mlp_size());
+    return mlp_train_device(feats, target, n, w.data(), 0, 0.0f, loss_out, grad_out, stream);
+}
+
+const char *perrk_last_error(void) { return g_err.c_str(); }
+
+const char *perrk_status_string(perrk_status s) {
+    switch (s) {
+        case PERRK_OK: return "ok";
+        case PERRK_INVALID_ARG: return "invalid argument";
+        case PERRK_CUDA_ERROR: return "CUDA error";
+        case PERRK_NONPHYSICAL_STATE: return "non-physical state";
+        case PERRK_TIMEOUT: return "timeout";
+        case PERRK_OUT_OF_MEMORY: return "out of memory";
+        case PERRK_NOT_SUPPORTED: return "not supported";
+    }
+    return "unknown status";
+}
+
+}  // extern "C"

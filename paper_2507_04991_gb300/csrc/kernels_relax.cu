@@ -1,0 +1,383 @@
+// Relaxation kernels (Sec. 3 and Sec. 3.1 of the paper), float64:
+//   k_relax_init   Delta H = dt sum_e e_dh[e] per instance; initial Newton guess
+//   k_newton_pass  one full-state pass at the current gamma:
+//                  R = sum omega J s(U_n + gamma dt d), G = sum omega J <w(.), dt d>,
+//                  then (last block of the instance) one Newton update of
+//                  r(gamma) = R - H_target(gamma) (eq. RelaxationEquation)
+//   k_update       U_{n+1} = U_n + gamma dt d (eq. RRKM_Update), t += gamma dt,
+//                  step record; H(U_{n+1}) recomputed only after a fallback
+//   k_entropy      H(U) and sum omega J |s(U)| per instance
+// Work is split into chunks of contiguous elements of one instance; each
+// chunk writes a compensated partial, and the last chunk of an instance to
+// finish (atomic ticket, no waiting) sums the partials in chunk order, so the
+// result is deterministic.  Passes of an instance whose Newton solve is done
+// return immediately, so a fixed number of launches (graph-capturable)
+// realises the data-dependent iteration count.
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "physics.cuh"
+
+namespace perrk {
+
+struct RelaxParams {
+    double *U;
+    const double *d, *e_dh, *wJ;
+    const int32_t *chunk_inst, *chunk_e0, *chunk_e1, *inst_chunk0, *inst_nchunks;
+    InstScalars *scal;
+    double *partials;      // [n_chunks][8]
+    uint32_t *counters;    // [n_inst]
+    uint32_t *flags;
+    perrk_step_info *rec;
+    const float *mlp;
+    int rec_slot, rec_cap, n_inst;
+    size_t NE;
+    double gamma_gas;
+    int max_it, guess, target, relax, query;
+    double tol_r, tol_g;
+};
+
+template <int DIM, int EQ>
+__device__ __forceinline__ void node_entropy(const double *u, double gam, double &s, double *w, uint32_t &bad) {
+    if constexpr (EQ == EQ_BURGERS) {
+        s = 0.5 * u[0] * u[0];
+        if (w) w[0] = u[0];
+    } else {
+        euler_entropy<DIM>(u, gam, s, w, bad);
+    }
+}
+
+// Write this block's NQ compensated sums, take a ticket; returns true in
+// thread 0 of the instance's last block, whose sums over all chunks (in chunk
+// order) are then in tot[].
+template <int NQ>
+__device__ __forceinline__ bool chunk_finish(const RelaxParams &P, int chunk, int inst, double (&s)[NQ], double (&c)[NQ],
+                                             double (&tot)[NQ]) {
+    __shared__ double sm[2 * NQ * 32];
+    __shared__ int s_last;
+    block_sum<NQ>(s, c, sm);
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < NQ; ++k) {
+            P.partials[(size_t)chunk * 8 + 2 * k] = s[k];
+            P.partials[(size_t)chunk * 8 + 2 * k + 1] = c[k];
+        }
+        __threadfence();
+        unsigned ticket = atomicAdd(P.counters + inst, 1u);
+        s_last = (ticket == (unsigned)P.inst_nchunks[inst] - 1u);
+    }
+    __syncthreads();
+    if (!s_last || threadIdx.x != 0) return false;
+    __threadfence();
+    const int c0 = P.inst_chunk0[inst], nc = P.inst_nchunks[inst];
+    for (int k = 0; k < NQ; ++k) {
+        double ss = 0.0, cc = 0.0;
+        for (int j = 0; j < nc; ++j) {
+            comp_add(ss, cc, __ldcg(P.partials + (size_t)(c0 + j) * 8 + 2 * k));
+            cc += __ldcg(P.partials + (size_t)(c0 + j) * 8 + 2 * k + 1);
+        }
+        tot[k] = ss + cc;
+    }
+    P.counters[inst] = 0u;
+    return true;
+}
+
+__device__ void accept_gamma(InstScalars &s) {
+    // Sec. 3.2.1: a non-converged Newton solve falls back to gamma = 1;
+    // roots outside (0.5, 1.5) are rejected as spurious (r(0) = 0 always).
+    if (!s.converged || !isfinite(s.gamma) || !(s.gamma > 0.5 && s.gamma < 1.5)) {
+        s.gamma = 1.0;
+        s.converged = 0;
+        s.flags |= PERRK_FLAG_NEWTON_FALLBACK;
+        s.need_H = !(s.iters > 0 && s.gamma_eval == 1.0);
+        if (!s.need_H) s.H_next = s.R_last;
+    } else {
+        s.need_H = 0;
+        s.H_next = (s.gamma == s.gamma_eval) ? s.R_last : fma(s.G_last, s.gamma - s.gamma_eval, s.R_last);
+    }
+}
+
+template <int DIM, int EQ>
+__global__ void k_relax_init(const RelaxParams P) {
+    constexpr int NP = ipow4(DIM);
+    const int chunk = blockIdx.x;
+    const int inst = P.chunk_inst[chunk];
+    double s[1] = {0.0}, c[1] = {0.0}, tot[1];
+    for (int e = P.chunk_e0[chunk] + threadIdx.x; e < P.chunk_e1[chunk]; e += blockDim.x) comp_add(s[0], c[0], P.e_dh[e]);
+    (void)NP;
+    if (!chunk_finish<1>(P, chunk, inst, s, c, tot)) return;
+    InstScalars &S = P.scal[inst];
+    S.dH = S.dt * tot[0];
+    S.iters = 0;
+    S.flags = 0;
+    S.converged = 0;
+    S.need_H = 0;
+    if (!P.relax) {
+        S.gamma = 1.0;
+        S.done = 1;
+        S.converged = 1;
+        S.gamma_guess = 1.0;
+        return;
+    }
+    S.gamma = (P.guess == PERRK_GUESS_ONE) ? 1.0 : S.hist_gamma[0];
+    S.gamma_guess = S.gamma;
+    S.gamma_eval = NAN;
+    S.done = 0;
+    if (P.max_it == 0) {
+        S.done = 1;
+        accept_gamma(S);
+    }
+}
+
+template <int DIM, int EQ>
+__global__ void __launch_bounds__(256) k_newton_pass(const RelaxParams P) {
+    constexpr int NP = ipow4(DIM);
+    constexpr int V = EQ == EQ_BURGERS ? 1 : DIM + 2;
+    const int chunk = blockIdx.x;
+    const int inst = P.chunk_inst[chunk];
+    if (P.scal[inst].done) return;       // uniform per block
+    const double gam = P.scal[inst].gamma, dt = P.scal[inst].dt, gdt = gam * dt;
+    const size_t NPtot = P.NE * NP;
+    const size_t n0 = (size_t)P.chunk_e0[chunk] * NP, n1 = (size_t)P.chunk_e1[chunk] * NP;
+    double s[3] = {0, 0, 0}, c[3] = {0, 0, 0}, tot[3];
+    uint32_t bad = 0;
+    for (size_t j = n0 + threadIdx.x; j < n1; j += blockDim.x) {
+        double u[V], dv[V], w[V], sv;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            dv[v] = __ldg(P.d + v * NPtot + j);
+            u[v] = fma(gdt, dv[v], __ldg(P.U + v * NPtot + j));
+        }
+        node_entropy<DIM, EQ>(u, P.gamma_gas, sv, w, bad);
+        double wd = 0.0;
+#pragma unroll
+        for (int v = 0; v < V; ++v) wd = fma(w[v], dv[v], wd);
+        const double wj = __ldg(P.wJ + j);
+        comp_add(s[0], c[0], wj * sv);
+        comp_add(s[1], c[1], wj * dt * wd);
+        comp_add(s[2], c[2], wj * fabs(sv));
+    }
+    if (bad) atomicOr(P.flags, bad);
+    if (!chunk_finish<3>(P, chunk, inst, s, c, tot)) return;
+    InstScalars &S = P.scal[inst];
+    const double R = tot[0], G = tot[1], A = tot[2];
+    double T, dT;
+    if (P.target == PERRK_TARGET_DELTA_H) {
+        T = fma(S.gamma, S.dH, S.H_n);
+        dT = S.dH;
+    } else if (P.target == PERRK_TARGET_PREV) {
+        T = S.H_n;
+        dT = 0.0;
+    } else {
+        T = S.H0;
+        dT = 0.0;
+    }
+    const double r = R - T, rp = G - dT;
+    S.iters += 1;
+    S.gamma_eval = S.gamma;
+    S.R_last = R;
+    S.G_last = G;
+    S.A_last = A;
+    if (fabs(r) <= P.tol_r * S.A_n) {
+        // no further pass; the correction from this pass is still applied
+        if (isfinite(r) && isfinite(rp) && rp != 0.0) S.gamma = S.gamma - r / rp;
+        S.converged = 1;
+        S.done = 1;
+    } else if (!isfinite(r) || !isfinite(rp) || rp == 0.0) {
+        S.done = 1;
+    } else {
+        const double dg = -r / rp;
+        S.gamma = S.gamma + dg;
+        if (fabs(dg) <= P.tol_g) {
+            S.converged = 1;
+            S.done = 1;
+        }
+    }
+    if (!S.done && S.iters >= P.max_it) S.done = 1;
+    if (S.done) accept_gamma(S);
+}
+
+template <int DIM, int EQ>
+__global__ void __launch_bounds__(256) k_update(const RelaxParams P) {
+    constexpr int NP = ipow4(DIM);
+    constexpr int V = EQ == EQ_BURGERS ? 1 : DIM + 2;
+    const int chunk = blockIdx.x;
+    const int inst = P.chunk_inst[chunk];
+    const double gdt = P.scal[inst].gamma * P.scal[inst].dt;
+    const int needH = P.scal[inst].need_H;
+    const size_t NPtot = P.NE * NP;
+    const size_t n0 = (size_t)P.chunk_e0[chunk] * NP, n1 = (size_t)P.chunk_e1[chunk] * NP;
+    double s[2] = {0, 0}, c[2] = {0, 0}, tot[2];
+    uint32_t bad = 0;
+    for (size_t j = n0 + threadIdx.x; j < n1; j += blockDim.x) {
+        double u[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            u[v] = fma(gdt, __ldg(P.d + v * NPtot + j), P.U[v * NPtot + j]);
+            P.U[v * NPtot + j] = u[v];
+            if (!isfinite(u[v])) bad |= PERRK_FLAG_NONFINITE;
+        }
+        if (needH) {
+            double sv;
+            node_entropy<DIM, EQ>(u, P.gamma_gas, sv, nullptr, bad);
+            const double wj = __ldg(P.wJ + j);
+            comp_add(s[0], c[0], wj * sv);
+            comp_add(s[1], c[1], wj * fabs(sv));
+        }
+    }
+    if (bad) atomicOr(P.flags, bad);
+    if (!chunk_finish<2>(P, chunk, inst, s, c, tot)) return;
+    InstScalars &S = P.scal[inst];
+    double Hn1, An1;
+    if (needH) {
+        Hn1 = tot[0];
+        An1 = tot[1];
+    } else if (P.relax) {
+        Hn1 = S.H_next;
+        An1 = S.A_last;
+    } else {
+        Hn1 = NAN;
+        An1 = S.A_n;
+    }
+    S.t += S.gamma * S.dt;
+    const uint32_t fl = S.flags | (*(volatile uint32_t *)P.flags);
+    if (P.rec) {
+        perrk_step_info &R = P.rec[(size_t)(S.nsteps_done % P.rec_cap) * P.n_inst + inst];
+        R.gamma = S.gamma;
+        R.H_n = S.H_n;
+        R.dH = S.dH;
+        R.H_next = Hn1;
+        R.t = S.t;
+        R.gamma_guess = S.gamma_guess;
+        R.newton_iters = S.iters;
+        R.flags = fl;
+    }
+    if (P.relax) {
+        if (S.converged) {
+            S.hist_gamma[2] = S.hist_gamma[1];
+            S.hist_gamma[1] = S.hist_gamma[0];
+            S.hist_gamma[0] = S.gamma;
+        }
+        S.hist_dh[2] = S.hist_dh[1];
+        S.hist_dh[1] = S.hist_dh[0];
+        S.hist_dh[0] = S.A_n > 0.0 ? S.dH / S.A_n : 0.0;
+    }
+    S.H_n = Hn1;
+    if (isfinite(An1)) S.A_n = An1;
+    S.nsteps_done += 1;
+}
+
+template <int DIM, int EQ>
+__global__ void __launch_bounds__(256) k_entropy(const RelaxParams P) {
+    constexpr int NP = ipow4(DIM);
+    constexpr int V = EQ == EQ_BURGERS ? 1 : DIM + 2;
+    const int chunk = blockIdx.x;
+    const int inst = P.chunk_inst[chunk];
+    const size_t NPtot = P.NE * NP;
+    const size_t n0 = (size_t)P.chunk_e0[chunk] * NP, n1 = (size_t)P.chunk_e1[chunk] * NP;
+    double s[2] = {0, 0}, c[2] = {0, 0}, tot[2];
+    uint32_t bad = 0;
+    for (size_t j = n0 + threadIdx.x; j < n1; j += blockDim.x) {
+        double u[V], sv;
+#pragma unroll
+        for (int v = 0; v < V; ++v) u[v] = __ldg(P.U + v * NPtot + j);
+        node_entropy<DIM, EQ>(u, P.gamma_gas, sv, nullptr, bad);
+        const double wj = __ldg(P.wJ + j);
+        comp_add(s[0], c[0], wj * sv);
+        comp_add(s[1], c[1], wj * fabs(sv));
+    }
+    if (bad) atomicOr(P.flags, bad);
+    if (!chunk_finish<2>(P, chunk, inst, s, c, tot)) return;
+    InstScalars &S = P.scal[inst];
+    if (P.query) {
+        S.H_next = tot[0];
+        return;
+    }
+    S.H_n = tot[0];
+    S.H0 = tot[0];
+    S.A_n = tot[1];
+    S.t = 0.0;
+    S.gamma = 1.0;
+    for (int k = 0; k < 3; ++k) {
+        S.hist_gamma[k] = 1.0;
+        S.hist_dh[k] = 0.0;
+    }
+    S.nsteps_done = 0;
+}
+
+// ------------------------------------------------------------------ launchers
+
+static RelaxParams relax_params(Ctx &c) {
+    RelaxParams P{};
+    P.U = c.U;
+    P.d = c.d;
+    P.e_dh = c.e_dh;
+    P.wJ = c.g_wJ;
+    P.chunk_inst = c.g_chunk_inst;
+    P.chunk_e0 = c.g_chunk_e0;
+    P.chunk_e1 = c.g_chunk_e1;
+    P.inst_chunk0 = c.g_inst_chunk0;
+    P.inst_nchunks = c.g_inst_nchunks;
+    P.scal = c.g_scal;
+    P.partials = c.g_partials;
+    P.counters = c.g_counters;
+    P.flags = c.g_flags;
+    P.rec = nullptr;
+    P.mlp = c.g_mlp;
+    P.n_inst = c.n_inst;
+    P.NE = (size_t)c.n_elem;
+    P.gamma_gas = c.gamma_gas;
+    P.max_it = c.opt.newton_max_it;
+    P.guess = c.opt.guess;
+    P.target = c.opt.target;
+    P.relax = c.opt.relaxation;
+    P.tol_r = c.opt.newton_tol_r;
+    P.tol_g = c.opt.newton_tol_g;
+    return P;
+}
+
+#define PERRK_RELAX_DISPATCH(NAME, KERNEL)                                                       \
+    static void NAME(Ctx &c, const RelaxParams &P, cudaStream_t st, int threads) {              \
+        const int nb = (int)c.chunk_inst.size();                                                 \
+        if (c.equation == PERRK_BURGERS_1D) KERNEL<1, EQ_BURGERS><<<nb, threads, 0, st>>>(P);   \
+        else if (c.dim == 1) KERNEL<1, EQ_EULER><<<nb, threads, 0, st>>>(P);                    \
+        else if (c.dim == 2) KERNEL<2, EQ_EULER><<<nb, threads, 0, st>>>(P);                    \
+        else KERNEL<3, EQ_EULER><<<nb, threads, 0, st>>>(P);                                    \
+    }
+PERRK_RELAX_DISPATCH(run_init, k_relax_init)
+PERRK_RELAX_DISPATCH(run_pass, k_newton_pass)
+PERRK_RELAX_DISPATCH(run_update, k_update)
+PERRK_RELAX_DISPATCH(run_entropy, k_entropy)
+#undef PERRK_RELAX_DISPATCH
+
+perrk_status launch_relax_init(Ctx &c, void *stream) {
+    RelaxParams P = relax_params(c);
+    run_init(c, P, (cudaStream_t)stream, 256);
+    return cuda_check((int)cudaGetLastError(), "relax_init launch");
+}
+
+perrk_status launch_newton_pass(Ctx &c, void *stream) {
+    RelaxParams P = relax_params(c);
+    run_pass(c, P, (cudaStream_t)stream, c.relax_threads);
+    return cuda_check((int)cudaGetLastError(), "newton_pass launch");
+}
+
+perrk_status launch_update(Ctx &c, int rec_slot, void *stream) {
+    RelaxParams P = relax_params(c);
+    P.rec = c.g_records;
+    P.rec_slot = rec_slot;
+    P.rec_cap = c.rec_cap;
+    run_update(c, P, (cudaStream_t)stream, c.relax_threads);
+    return cuda_check((int)cudaGetLastError(), "update launch");
+}
+
+perrk_status launch_entropy(Ctx &c, int query, void *stream) {
+    RelaxParams P = relax_params(c);
+    P.query = query;
+    run_entropy(c, P, (cudaStream_t)stream, c.relax_threads);
+    return cuda_check((int)cudaGetLastError(), "entropy launch");
+}
+
+perrk_status launch_entropy_set(Ctx &c, void *stream) { return launch_entropy(c, 0, stream); }
+
+}  // namespace perrk

@@ -1,0 +1,24 @@
+// Instantiations of the P-ERK stage kernel for 2D meshes (split per dimension
+// so that the translation units compile in parallel).
+#include <cuda_runtime.h>
+
+#include "stage.cuh"
+
+namespace perrk {
+
+template <int EQ, typename Real, bool CURVED>
+static cudaError_t go(const StageParams &P, int epb, int grid, cudaStream_t st) {
+    if (epb == 4) { k_stage<2, EQ, Real, CURVED, 4><<<grid, 4 * ipow4(2), 0, st>>>(P); return cudaGetLastError(); }
+    if (epb == 8) { k_stage<2, EQ, Real, CURVED, 8><<<grid, 8 * ipow4(2), 0, st>>>(P); return cudaGetLastError(); }
+    if (epb == 16) { k_stage<2, EQ, Real, CURVED, 16><<<grid, 16 * ipow4(2), 0, st>>>(P); return cudaGetLastError(); }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t stage_launch_2d(const StageParams &P, bool burgers, bool mixed, bool curved, int epb, int grid, cudaStream_t st) {
+    (void)burgers;
+    if (curved) { if (mixed) return go<EQ_EULER, float, true>(P, epb, grid, st); return go<EQ_EULER, double, true>(P, epb, grid, st); }
+    if (mixed) return go<EQ_EULER, float, false>(P, epb, grid, st);
+    return go<EQ_EULER, double, false>(P, epb, grid, st);
+}
+
+}  // namespace perrk

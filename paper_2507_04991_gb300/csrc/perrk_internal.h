@@ -1,0 +1,157 @@
+// Internal types of libperrk shared by the host setup and the CUDA translation units.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/perrk.h"
+
+namespace perrk {
+
+constexpr int kMaxDim = 3;
+constexpr int kNodes1D = 4;                 // N + 1 with N = 3
+constexpr int kMaxR = 64;                   // partitions per instance
+constexpr int kMlpHidden = 64;
+constexpr int kMlpFeatures = 6;
+
+#ifdef __CUDACC__
+#define PERRK_HD __host__ __device__
+#else
+#define PERRK_HD
+#endif
+
+PERRK_HD inline constexpr int ipow4(int d) { return d == 0 ? 1 : 4 * ipow4(d - 1); }
+
+// Per (stage, global partition) coefficients of the low-storage stage row,
+// already multiplied by the instance's dt: U_{n,i} = U_n + a1 K_1 + asub K_{i-1}.
+struct StageCoef {
+    double a1;
+    double asub;
+    double b;        // b_i of the instance (the direction d += b K_i)
+    double first_b;  // 1.0 at the instance's first stage with b != 0
+};
+
+struct StageCoefF {
+    float a1;
+    float asub;
+};
+
+// Per-instance relaxation scalars, resident in device memory.
+struct InstScalars {
+    double dt;
+    double t;
+    double H_n;        // H(U_n)
+    double A_n;        // sum omega J |s(U_n)| (tolerance scale)
+    double H0;         // H(U_0)
+    double dH;         // Delta H of the current step
+    double gamma;      // current Newton iterate / accepted gamma
+    double gamma_eval; // gamma of the last full-state pass
+    double R_last;     // H(U_n + gamma_eval dt d)
+    double G_last;     // <w(U_n + gamma_eval dt d), dt d>
+    double A_last;     // sum omega J |s| at gamma_eval
+    double gamma_guess;
+    double hist_gamma[3];  // gamma_{n-1}, gamma_{n-2}, gamma_{n-3}
+    double hist_dh[3];     // (Delta H / A)_{n}, _{n-1}, _{n-2} after the step
+    double H_next;
+    int32_t iters;
+    int32_t done;
+    int32_t converged;
+    int32_t need_H;
+    uint32_t flags;
+    int32_t nsteps_done;
+};
+
+struct HostMesh {
+    int dim = 0, n_elem = 0;
+    std::vector<double> coords;      // [n_elem][NP][dim]
+    std::vector<int32_t> faces;      // [n_faces][4]
+    std::vector<int32_t> part;       // local partition id
+};
+
+struct Instance {
+    int elem0 = 0, n_elem = 0;       // element range in the concatenated numbering
+    int gp0 = 0, R = 0;              // global partition ids gp0 .. gp0+R-1
+    int S = 0, p = 0;
+    std::vector<int> E;
+    std::vector<double> c, b, a1, asub;  // local tableau, a1/asub [R][S]
+    double dt = 0.0;
+    int chunk0 = 0, n_chunks = 0;    // relaxation work chunks
+};
+
+struct Ctx {
+    // shape
+    int dim = 0, NP = 0, V = 0, n_elem = 0, n_inst = 0, S = 0, p = 0, n_gp = 0;
+    int equation = 0, surface = 0;
+    double gamma_gas = 1.4;
+    bool curved = false;
+    perrk_options opt{};
+    std::vector<Instance> inst;
+    std::vector<int32_t> gp_of_elem;          // [n_elem]
+    std::vector<int32_t> E_of_gp;             // [n_gp]
+    std::vector<int32_t> elist;               // elements sorted by E descending
+    std::vector<int32_t> n_active;            // [S] active prefix length per stage
+    std::vector<int32_t> any_b;               // [S] 1 if some instance has b_i != 0
+    std::vector<int32_t> chunk_inst, chunk_e0, chunk_e1;
+    int chunk_elems = 0;
+    // host geometry (double)
+    std::vector<double> lgl_w;                // [4]
+    std::vector<double> lgl_D;                // [4][4]
+    std::vector<double> geo_node;             // curved: [6][n_elem][NP] = Ja11 Ja12 Ja21 Ja22 invJ wJ
+    std::vector<double> geo_elem;             // box: [n_elem][8] = Ja_kk (dim) , invJ, J
+    std::vector<double> fnorm;                // curved: [n_elem][4][4][2]; box: [n_elem][2 dim]
+    std::vector<double> wJ;                   // [n_elem][NP] omega_q J_q (always)
+    std::vector<int32_t> nbr;                 // [n_elem][2 dim]
+
+    // device buffers
+    double *U = nullptr, *K1 = nullptr, *Ka = nullptr, *Kb = nullptr, *d = nullptr;
+    double *e_dh = nullptr;                   // [n_elem] per-element b-weighted <w, K> sums
+    double *g_node = nullptr, *g_elem = nullptr, *g_fnorm = nullptr, *g_wJ = nullptr;
+    int32_t *g_nbr = nullptr, *g_gp = nullptr, *g_elist = nullptr;
+    int32_t *g_chunk_inst = nullptr, *g_chunk_e0 = nullptr, *g_chunk_e1 = nullptr;
+    int32_t *g_inst_chunk0 = nullptr, *g_inst_nchunks = nullptr;
+    StageCoef *g_coef = nullptr;              // [S][n_gp]
+    StageCoefF *g_coef_f = nullptr;           // [S][n_gp]
+    InstScalars *g_scal = nullptr;            // [n_inst]
+    double *g_partials = nullptr;             // [n_chunks][8]
+    uint32_t *g_counters = nullptr;           // [n_inst]
+    uint32_t *g_flags = nullptr;              // [1]
+    perrk_step_info *g_records = nullptr;     // [rec_cap][n_inst]
+    int rec_cap = 0;
+    float *g_mlp = nullptr;                   // weights (nullptr: no MLP)
+    int mlp_on = 0;
+
+    // launch configuration (autotuned)
+    int stage_epb = 0;                        // elements per CTA in the stage kernel
+    int stage_persistent = 0;                 // grid = min(groups, persistent blocks)
+    int relax_threads = 256;
+    bool tuned = false;
+
+    // CUDA graph of one step
+    void *graph_exec = nullptr;               // cudaGraphExec_t
+    void *graph = nullptr;                    // cudaGraph_t
+    bool graph_dirty = true;
+};
+
+// host setup (setup.cpp)
+void lgl_tables(std::vector<double> &x, std::vector<double> &w, std::vector<double> &D);
+perrk_status build_ctx(Ctx &c, int n, const perrk_mesh_desc *mesh, const perrk_scheme_desc *scheme,
+                       const perrk_options *opts, std::string &err);
+void stage_coefficients(const Ctx &c, std::vector<StageCoef> &coef, std::vector<StageCoefF> &coef_f);
+
+// device side (kernels_*.cu)
+perrk_status launch_stage(Ctx &c, int stage, const double *U, double *Kout, const double *Kprev,
+                          bool rhs_only, void *stream);
+perrk_status launch_relax_init(Ctx &c, void *stream);
+perrk_status launch_newton_pass(Ctx &c, void *stream);
+perrk_status launch_update(Ctx &c, int rec_slot, void *stream);
+perrk_status launch_entropy_set(Ctx &c, void *stream);
+perrk_status launch_entropy(Ctx &c, int query, void *stream);
+perrk_status launch_mlp_guess(Ctx &c, void *stream);
+perrk_status mlp_train_device(const float *feats, const float *target, int n, float *weights, int epochs,
+                              float lr, float *loss, float *grad_out, void *stream);
+
+void set_error(const std::string &e);
+perrk_status cuda_check(int err, const char *what);
+
+}  // namespace perrk

@@ -1,0 +1,345 @@
+// P-ERK stage kernel: for the elements active at stage i (a prefix of the
+// partition-major element list) evaluate
+//   U_{n,i} = U_n + a1 K_1 + asub K_{i-1}              (low-storage stage row, dt folded in)
+//   J_q K_{i,q} = - sum_k sum_m 2 D_{qm} f#(U_q, U_m; avg Ja^k)     (flux differencing)
+//                 - sum_{faces} (1/omega) (f*(U-, U+; nu) - f(U_q).nu)  (surface lift)
+// (Sec. 2.1-2.2, eq. PartitionedRKSystem; DGSEM with EC volume flux and EC/ES
+// surface flux) and, at stages with b_i != 0, the per-element entropy
+// integrand b_i sum_q omega_q J_q <w(U_{n,i,q}), K_{i,q}> (eq.
+// EntropyChange_EntropyVariables_ReArranged) and d += b_i K_i (Sec. 3).
+//
+// Layout: one thread per node, EPB elements per CTA; state SoA [V][NE][NP]
+// float64.  Neighbour face traces are recomputed from the neighbour's U_n,
+// K_1, K_{i-1} with the neighbour's own stage row (an inactive neighbour has
+// the row (c_i dt, 0): the cheap update of eq. InternalConsistency).  An
+// interface flux is always evaluated as f*(U_plus_side, U_minus_side; nu of
+// the '+' side), so both elements compute bit-identical values.
+#pragma once
+
+#include "physics.cuh"
+
+namespace perrk {
+
+struct StageParams {
+    const double *U, *K1, *Kprev;
+    double *Kout, *d, *e_dh;
+    const int32_t *elist, *nbr, *gp;
+    const StageCoef *coef;      // [n_gp] rows of this stage
+    const StageCoefF *coef_f;
+    const double *g_node, *g_elem, *fnorm, *wJ;
+    size_t NE;
+    int n_active;
+    int stage1;                 // U_{n,1} = U_n: no K loads
+    int do_b;                   // some element has b_i != 0 at this stage
+    int es;                     // Rusanov dissipation on the surface flux
+    double gamma_gas;
+    double D[16];
+    double w_end;
+    uint32_t *flags;
+};
+
+template <int DIM>
+__device__ __forceinline__ int face_pos(int q, int k) {
+    const int i0 = q & 3, i1 = (q >> 2) & 3, i2 = (q >> 4) & 3;
+    if (DIM == 1) return 0;
+    if (DIM == 2) return k == 0 ? i1 : i0;
+    return k == 0 ? (i1 + 4 * i2) : (k == 1 ? (i0 + 4 * i2) : (i0 + 4 * i1));
+}
+
+template <int DIM>
+__device__ __forceinline__ int face_node_dev(int f, int kk) {
+    const int k = f >> 1, ed = (f & 1) ? 3 : 0;
+    if (DIM == 1) return ed;
+    if (DIM == 2) return k == 0 ? ed + 4 * kk : kk + 4 * ed;
+    const int a = kk & 3, b = kk >> 2;
+    return k == 0 ? ed + 4 * a + 16 * b : (k == 1 ? a + 4 * ed + 16 * b : a + 4 * b + 16 * ed);
+}
+
+// Stage-row combination at one node; the same instruction sequence is used
+// for an element's own nodes and for its neighbours' face nodes.
+template <int V, typename Real>
+__device__ __forceinline__ void stage_state(const StageParams &P, size_t NPtot, size_t idx, int g, Real *u, double *Ud,
+                                            double *K1d, double *Kpd) {
+    if (P.stage1) {
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            Ud[v] = __ldg(P.U + v * NPtot + idx);
+            K1d[v] = 0.0;
+            Kpd[v] = 0.0;
+            u[v] = (Real)Ud[v];
+        }
+        return;
+    }
+    const StageCoef c = P.coef[g];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        Ud[v] = __ldg(P.U + v * NPtot + idx);
+        K1d[v] = __ldg(P.K1 + v * NPtot + idx);
+        Kpd[v] = (c.asub != 0.0) ? __ldg(P.Kprev + v * NPtot + idx) : 0.0;
+    }
+    if constexpr (sizeof(Real) == 8) {
+#pragma unroll
+        for (int v = 0; v < V; ++v) u[v] = (Real)fma(c.asub, Kpd[v], fma(c.a1, K1d[v], Ud[v]));
+    } else {
+        const StageCoefF cf = P.coef_f[g];
+#pragma unroll
+        for (int v = 0; v < V; ++v) u[v] = (Real)fmaf(cf.asub, (float)Kpd[v], fmaf(cf.a1, (float)K1d[v], (float)Ud[v]));
+    }
+}
+
+template <int DIM, int EQ, typename Real, bool CURVED, int EPB>
+__global__ void __launch_bounds__(EPB * ipow4(DIM)) k_stage(const StageParams P) {
+    constexpr int NP = ipow4(DIM), NF = 2 * DIM, NFP = ipow4(DIM - 1);
+    constexpr int V = EQ == EQ_BURGERS ? 1 : DIM + 2;
+    constexpr int NPR = EQ == EQ_BURGERS ? 1 : DIM + 5;
+    __shared__ Real s_u[EPB][V][NP];
+    __shared__ Real s_pr[EPB][NPR][NP];
+    __shared__ Real s_sf[EPB][NF * NFP][V];
+    __shared__ Real s_ja[EPB][CURVED ? 4 : 1][NP];
+    __shared__ double s_red[EPB][NP];
+
+    const int el = threadIdx.x / NP, q = threadIdx.x % NP;
+    const size_t NPtot = P.NE * NP;
+    const Real gm1 = Real(P.gamma_gas - 1.0), inv_gm1 = Real(1.0 / (P.gamma_gas - 1.0)), gam = Real(P.gamma_gas);
+    const Real inv_w = Real(1.0 / P.w_end);
+    uint32_t bad = 0;
+    const int ngroups = (P.n_active + EPB - 1) / EPB;
+
+    for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
+        const int slot = grp * EPB + el;
+        const bool valid = slot < P.n_active;
+        const int e = P.elist[valid ? slot : P.n_active - 1];
+        const int g = P.gp[e];
+        const size_t idx = (size_t)e * NP + q;
+
+        // ---- A: own stage state
+        Real u[V];
+        double Ud[V], K1d[V], Kpd[V];
+        stage_state<V, Real>(P, NPtot, idx, g, u, Ud, K1d, Kpd);
+#pragma unroll
+        for (int v = 0; v < V; ++v) s_u[el][v][q] = u[v];
+        if constexpr (EQ == EQ_EULER) {
+            Prim<Real, (EQ == EQ_EULER ? DIM : 1)> pr = make_prim<Real, (EQ == EQ_EULER ? DIM : 1)>(u, gm1, bad);
+            s_pr[el][0][q] = pr.rho;
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) s_pr[el][1 + a][q] = pr.v[a];
+            s_pr[el][DIM + 1][q] = pr.p;
+            s_pr[el][DIM + 2][q] = pr.beta;
+            s_pr[el][DIM + 3][q] = pr.lrho;
+            s_pr[el][DIM + 4][q] = pr.lbeta;
+        }
+        Real invJ, Jak_box[DIM > 0 ? DIM : 1];
+        if constexpr (CURVED) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) s_ja[el][c][q] = (Real)__ldg(P.g_node + c * NPtot + idx);
+            invJ = (Real)__ldg(P.g_node + 4 * NPtot + idx);
+        } else {
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) Jak_box[a] = (Real)__ldg(P.g_elem + (size_t)e * 8 + a);
+            invJ = (Real)__ldg(P.g_elem + (size_t)e * 8 + 3);
+        }
+        __syncthreads();
+
+        // ---- B: interface fluxes at this element's face nodes
+        for (int sl = q; sl < NF * NFP; sl += NP) {
+            const int f = sl / NFP, kk = sl % NFP;
+            const int qs = face_node_dev<DIM>(f, kk);
+            const int nb = P.nbr[(size_t)e * NF + f];
+            const int qn = face_node_dev<DIM>(f ^ 1, kk);
+            Real un[V];
+            double t0[V], t1[V], t2[V];
+            stage_state<V, Real>(P, NPtot, (size_t)nb * NP + qn, P.gp[nb], un, t0, t1, t2);
+            Real us[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) us[v] = s_u[el][v][qs];
+            Real nrm[DIM];
+            if constexpr (CURVED) {
+                nrm[0] = (Real)__ldg(P.fnorm + (((size_t)e * NF + f) * NFP + kk) * 2 + 0);
+                nrm[1 % DIM] = (Real)__ldg(P.fnorm + (((size_t)e * NF + f) * NFP + kk) * 2 + 1);
+            } else {
+                nrm[0] = (Real)__ldg(P.fnorm + (size_t)e * NF + f);
+            }
+            const bool self_plus = (f & 1);
+            const Real *uL = self_plus ? us : un;
+            const Real *uR = self_plus ? un : us;
+            Real fs[V], fp[V];
+            if constexpr (EQ == EQ_BURGERS) {
+                const Real a = uL[0], b = uR[0];
+                fs[0] = (a * a + a * b + b * b) * Real(1.0 / 6.0) * nrm[0];
+                if (P.es) {
+                    Real lam = fmax(fabs(a), fabs(b)) * fabs(nrm[0]);
+                    fs[0] -= Real(0.5) * lam * (b - a);
+                }
+                fp[0] = Real(0.5) * us[0] * us[0] * nrm[0];
+            } else {
+                constexpr int DD = EQ == EQ_EULER ? DIM : 1;
+                Prim<Real, DD> ps, pn;
+                ps.rho = s_pr[el][0][qs];
+#pragma unroll
+                for (int a = 0; a < DD; ++a) ps.v[a] = s_pr[el][1 + a][qs];
+                ps.p = s_pr[el][DD + 1][qs];
+                ps.beta = s_pr[el][DD + 2][qs];
+                ps.lrho = s_pr[el][DD + 3][qs];
+                ps.lbeta = s_pr[el][DD + 4][qs];
+                pn = make_prim<Real, DD>(un, gm1, bad);
+                const Prim<Real, DD> &PL = self_plus ? ps : pn;
+                const Prim<Real, DD> &PR = self_plus ? pn : ps;
+                const int k = f >> 1;
+                if constexpr (CURVED) {
+                    ranocha<Real, DD, -1>(PL, PR, nrm, inv_gm1, fs);
+                    euler_flux<Real, DD, -1>(us, ps, nrm, fp);
+                    if (P.es) {
+                        Real lam = max_speed<Real, DD, -1>(PL, PR, nrm, gam);
+#pragma unroll
+                        for (int v = 0; v < V; ++v) fs[v] -= Real(0.5) * lam * (uR[v] - uL[v]);
+                    }
+                } else {
+#define PERRK_AXIS_CASE(KK)                                                                   \
+    if (k == KK) {                                                                            \
+        ranocha<Real, DD, (KK < DD ? KK : 0)>(PL, PR, nrm, inv_gm1, fs);                      \
+        euler_flux<Real, DD, (KK < DD ? KK : 0)>(us, ps, nrm, fp);                            \
+        if (P.es) {                                                                           \
+            Real lam = max_speed<Real, DD, (KK < DD ? KK : 0)>(PL, PR, nrm, gam);            \
+            for (int v = 0; v < V; ++v) fs[v] -= Real(0.5) * lam * (uR[v] - uL[v]);           \
+        }                                                                                     \
+    }
+                    PERRK_AXIS_CASE(0)
+                    if (DIM > 1) PERRK_AXIS_CASE(1)
+                    if (DIM > 2) PERRK_AXIS_CASE(2)
+#undef PERRK_AXIS_CASE
+                }
+            }
+            const Real sg = self_plus ? Real(1) : Real(-1);
+#pragma unroll
+            for (int v = 0; v < V; ++v) s_sf[el][sl][v] = sg * (fs[v] - fp[v]) * inv_w;
+        }
+
+        // ---- C: volume flux differencing along each reference direction
+        Real acc[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[v] = 0;
+        const int id[3] = {q & 3, (q >> 2) & 3, (q >> 4) & 3};
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) {
+            const int ik = id[k];
+            const int stride = 1 << (2 * k);
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const int qm = q + (m - ik) * stride;
+                const Real Dv = Real(2.0) * (Real)P.D[ik * 4 + m];
+                Real F[V];
+                if constexpr (EQ == EQ_BURGERS) {
+                    const Real a = u[0], b = s_u[el][0][qm];
+                    if (m == ik) {
+                        if (ik != 0 && ik != 3) continue;
+                        F[0] = Real(0.5) * a * a;
+                    } else {
+                        F[0] = (a * a + a * b + b * b) * Real(1.0 / 6.0);
+                    }
+                    F[0] *= (CURVED ? Real(1) : Jak_box[0]);
+                } else {
+                    constexpr int DD = EQ == EQ_EULER ? DIM : 1;
+                    Prim<Real, DD> pq, pm;
+                    pq.rho = s_pr[el][0][q];
+                    pm.rho = s_pr[el][0][qm];
+#pragma unroll
+                    for (int a = 0; a < DD; ++a) {
+                        pq.v[a] = s_pr[el][1 + a][q];
+                        pm.v[a] = s_pr[el][1 + a][qm];
+                    }
+                    pq.p = s_pr[el][DD + 1][q];
+                    pm.p = s_pr[el][DD + 1][qm];
+                    pq.beta = s_pr[el][DD + 2][q];
+                    pm.beta = s_pr[el][DD + 2][qm];
+                    pq.lrho = s_pr[el][DD + 3][q];
+                    pm.lrho = s_pr[el][DD + 3][qm];
+                    pq.lbeta = s_pr[el][DD + 4][q];
+                    pm.lbeta = s_pr[el][DD + 4][qm];
+                    Real nv[DD];
+                    if constexpr (CURVED) {
+                        nv[0] = Real(0.5) * (s_ja[el][2 * k][q] + s_ja[el][2 * k][qm]);
+                        nv[1 % DD] = Real(0.5) * (s_ja[el][2 * k + 1][q] + s_ja[el][2 * k + 1][qm]);
+                    } else {
+                        nv[0] = Jak_box[k];
+                    }
+                    if (m == ik) {
+                        if (ik != 0 && ik != 3) continue;
+                        if constexpr (CURVED) euler_flux<Real, DD, -1>(u, pq, nv, F);
+                        else if (k == 0) euler_flux<Real, DD, 0>(u, pq, nv, F);
+                        else if (k == 1) euler_flux<Real, DD, (1 < DD ? 1 : 0)>(u, pq, nv, F);
+                        else euler_flux<Real, DD, (2 < DD ? 2 : 0)>(u, pq, nv, F);
+                    } else {
+                        if constexpr (CURVED) ranocha<Real, DD, -1>(pq, pm, nv, inv_gm1, F);
+                        else if (k == 0) ranocha<Real, DD, 0>(pq, pm, nv, inv_gm1, F);
+                        else if (k == 1) ranocha<Real, DD, (1 < DD ? 1 : 0)>(pq, pm, nv, inv_gm1, F);
+                        else ranocha<Real, DD, (2 < DD ? 2 : 0)>(pq, pm, nv, inv_gm1, F);
+                    }
+                }
+#pragma unroll
+                for (int v = 0; v < V; ++v) acc[v] = dfma(Dv, F[v], acc[v]);
+            }
+        }
+        __syncthreads();
+
+        // ---- D: surface terms, then K = -acc / J
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) {
+            const int ik = id[k];
+            if (ik == 0 || ik == 3) {
+                const int f = 2 * k + (ik == 3 ? 1 : 0);
+                const int sl = f * NFP + face_pos<DIM>(q, k);
+#pragma unroll
+                for (int v = 0; v < V; ++v) acc[v] += s_sf[el][sl][v];
+            }
+        }
+        double Kd[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            Kd[v] = -(double)acc[v] * (double)invJ;
+            if (!isfinite(Kd[v])) bad |= PERRK_FLAG_NONFINITE;
+            if (valid) P.Kout[v * NPtot + idx] = Kd[v];
+        }
+
+        // ---- E: stages with b_i != 0: entropy integrand and direction
+        if (P.do_b) {
+            const StageCoef c = P.coef[g];
+            double wdot = 0.0;
+            if (c.b != 0.0) {
+                double Ui[V];
+#pragma unroll
+                for (int v = 0; v < V; ++v) Ui[v] = P.stage1 ? Ud[v] : fma(c.asub, Kpd[v], fma(c.a1, K1d[v], Ud[v]));
+                if constexpr (EQ == EQ_BURGERS) {
+                    wdot = Ui[0] * Kd[0];
+                } else {
+                    constexpr int DD = EQ == EQ_EULER ? DIM : 1;
+                    double s, w[DD + 2];
+                    euler_entropy<DD>(Ui, P.gamma_gas, s, w, bad);
+#pragma unroll
+                    for (int v = 0; v < V; ++v) wdot = fma(w[v], Kd[v], wdot);
+                }
+                wdot *= __ldg(P.wJ + idx);
+                if (valid) {
+#pragma unroll
+                    for (int v = 0; v < V; ++v) {
+                        double dold = (c.first_b != 0.0) ? 0.0 : P.d[v * NPtot + idx];
+                        P.d[v * NPtot + idx] = fma(c.b, Kd[v], dold);
+                    }
+                }
+            }
+            s_red[el][q] = wdot;
+            __syncthreads();
+            if (q == 0 && valid && c.b != 0.0) {
+                double sacc = 0.0;
+                for (int j = 0; j < NP; ++j) sacc += s_red[el][j];
+                double old = (c.first_b != 0.0) ? 0.0 : P.e_dh[e];
+                P.e_dh[e] = fma(c.b, sacc, old);
+            }
+        }
+        __syncthreads();
+    }
+    if (__syncthreads_or(bad != 0)) {
+        if (bad) atomicOr(P.flags, bad);
+    }
+}
+
+}  // namespace perrk

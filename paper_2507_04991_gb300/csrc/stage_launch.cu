@@ -1,0 +1,65 @@
+// Launch of one P-ERK stage (or one plain RHS evaluation) over the active
+// element prefix of the partition-major element list.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "stage.cuh"
+
+namespace perrk {
+
+cudaError_t stage_launch_1d(const StageParams &, bool, bool, bool, int, int, cudaStream_t);
+cudaError_t stage_launch_2d(const StageParams &, bool, bool, bool, int, int, cudaStream_t);
+cudaError_t stage_launch_3d(const StageParams &, bool, bool, bool, int, int, cudaStream_t);
+
+int default_epb(int dim) { return dim == 1 ? 32 : (dim == 2 ? 8 : 2); }
+
+perrk_status launch_stage(Ctx &c, int stage, const double *U, double *Kout, const double *Kprev, bool rhs_only,
+                          void *stream) {
+    StageParams P{};
+    P.U = U;
+    P.K1 = c.K1;
+    P.Kprev = Kprev;
+    P.Kout = Kout;
+    P.d = c.d;
+    P.e_dh = c.e_dh;
+    P.elist = c.g_elist;
+    P.nbr = c.g_nbr;
+    P.gp = c.g_gp;
+    P.coef = c.g_coef + (size_t)stage * c.n_gp;
+    P.coef_f = c.g_coef_f + (size_t)stage * c.n_gp;
+    P.g_node = c.g_node;
+    P.g_elem = c.g_elem;
+    P.fnorm = c.g_fnorm;
+    P.wJ = c.g_wJ;
+    P.NE = (size_t)c.n_elem;
+    P.n_active = rhs_only ? c.n_elem : c.n_active[stage];
+    P.stage1 = (stage == 0 || rhs_only) ? 1 : 0;
+    P.do_b = (!rhs_only && c.any_b[stage]) ? 1 : 0;
+    P.es = c.surface == PERRK_SURFACE_ES_RUSANOV ? 1 : 0;
+    P.gamma_gas = c.gamma_gas;
+    for (int i = 0; i < 16; ++i) P.D[i] = c.lgl_D[i];
+    P.w_end = c.lgl_w[0];
+    P.flags = c.g_flags;
+    if (P.n_active <= 0) return PERRK_OK;
+    if (c.curved && c.dim != 2) {
+        set_error("curved geometry is only implemented in 2D");
+        return PERRK_NOT_SUPPORTED;
+    }
+    if ((c.curved && (!c.g_node || !c.g_fnorm)) || (!c.curved && (!c.g_elem || !c.g_fnorm))) {
+        set_error("geometry tables missing for the selected geometry mode");
+        return PERRK_INVALID_ARG;
+    }
+    const int epb = c.stage_epb > 0 ? c.stage_epb : default_epb(c.dim);
+    const int groups = (P.n_active + epb - 1) / epb;
+    int grid = groups;
+    if (c.stage_persistent > 0) grid = std::min(groups, c.stage_persistent);
+    const bool burgers = c.equation == PERRK_BURGERS_1D, mixed = c.opt.precision == PERRK_MIXED;
+    cudaError_t e;
+    if (c.dim == 1) e = stage_launch_1d(P, burgers, mixed, c.curved, epb, grid, (cudaStream_t)stream);
+    else if (c.dim == 2) e = stage_launch_2d(P, burgers, mixed, c.curved, epb, grid, (cudaStream_t)stream);
+    else e = stage_launch_3d(P, burgers, mixed, c.curved, epb, grid, (cudaStream_t)stream);
+    return cuda_check((int)e, "stage launch");
+}
+
+}  // namespace perrk

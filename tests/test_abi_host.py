@@ -1,0 +1,89 @@
+"""Host-side checks of the C ABI (no GPU): library loads, every declared entry
+point is exported, the library's tableau builder agrees with the oracle's, and
+malformed input is rejected before any device work."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2507_04991_gb300 as pk
+import workloads
+from oracle import tableau as T
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+    __graft_entry__.build()
+    return pk.load()
+
+
+def test_exports_every_declared_symbol(lib):
+    hdr = open(os.path.join(ROOT, "include", "perrk.h")).read()
+    declared = set(re.findall(r"\b(perrk_[a-z_0-9]+)\s*\(", hdr))
+    assert len(declared) >= 15
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert set(pk.EXPORTED) == declared
+
+
+@pytest.mark.parametrize("p,E", [(2, [8, 4]), (2, [16, 12, 8, 4, 2]), (3, [12, 6, 3]), (3, [8, 4]), (3, [3]),
+                                 (4, [16, 10, 7, 5]), (4, [5]), (2, [2])])
+def test_tableau_builder_matches_oracle(lib, p, E):
+    c, b, a1, asub = pk.perrk_build_tableau(p, E)
+    oc, ob, As = T.family(p, E)
+    S = len(oc)
+    assert np.abs(c - oc).max() < 1e-15 and np.abs(b - ob).max() == 0.0
+    for r, A in enumerate(As):
+        for i in range(1, S):
+            full = np.zeros(S)
+            full[0] += a1[r, i]
+            full[i - 1] += asub[r, i]
+            assert np.abs(full - A[i]).max() < 1e-15, (r, i)
+
+
+def _small_mesh():
+    wl = workloads.small_box_2d(n=4, seed=1, R=2, E=[6, 3], order=3)
+    keep = pk._Keep()
+    m = pk.mesh_desc(wl.coords, wl.faces, wl.part, keep)
+    tab = pk.perrk_build_tableau(3, [6, 3])
+    return wl, keep, m, tab
+
+
+@pytest.mark.parametrize("breakage", ["bad_rowsum", "bad_E", "bad_part", "bad_face", "bad_b", "bad_N", "asub_inactive"])
+def test_invalid_input_rejected(lib, breakage):
+    wl, keep, m, (c, b, a1, asub) = _small_mesh()
+    c, b, a1, asub = c.copy(), b.copy(), a1.copy(), asub.copy()
+    E = [6, 3]
+    part = wl.part.copy()
+    faces = wl.faces.copy()
+    if breakage == "bad_rowsum":
+        a1[0, 3] += 1e-6
+    elif breakage == "bad_E":
+        E = [6, 2]
+    elif breakage == "bad_part":
+        part[0] = 5
+    elif breakage == "bad_face":
+        faces[0, 3] = 2
+    elif breakage == "bad_b":
+        b[1] = 0.1
+    elif breakage == "asub_inactive":
+        asub[1, 2] = 0.01
+        a1[1, 2] -= 0.01
+    m = pk.mesh_desc(wl.coords, faces, part, keep)
+    if breakage == "bad_N":
+        m.N = 4
+    s = pk.scheme_desc(3, E, c, b, a1, asub, pk.EULER_2D, pk.SURFACE_ES_RUSANOV, 1.4, keep)
+    with pytest.raises(pk.PerrkError) as ei:
+        pk.perrk_create(m, s, pk.options())
+    assert ei.value.status == pk.PERRK_INVALID_ARG
+    assert pk.last_error()
+
+
+def test_status_strings(lib):
+    assert pk.status_string(0) == "ok"
+    assert pk.status_string(3) == "non-physical state"
+    assert pk.perrk_mlp_size() == 64 * 6 + 64 + 64 * 64 + 64 + 64 + 1 + 2 * 6 + 1

