@@ -291,7 +291,8 @@ def run_native(args):
 
     if rank != 0:
         return
-    cpu_val, cpu_steps, cpu_sec = oracle_sample(wl, steps=8, seconds_cap=25.0)
+    cpu_val, cpu_steps, cpu_sec = (oracle_sample(wl, steps=args.cpu_sample_steps, seconds_cap=25.0)
+                                   if args.cpu_sample_steps > 0 else (None, 0, 0.0))
     rel = float(np.abs(u_c - u_p).max() / np.abs(u_p).max())
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -327,6 +328,7 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="vortex2d")
     ap.add_argument("--max-it", type=int, default=4)
+    ap.add_argument("--cpu-sample-steps", type=int, default=8)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

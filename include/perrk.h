@@ -216,6 +216,11 @@ perrk_status perrk_mlp_train(const float *feats, const float *target, int n, flo
 perrk_status perrk_mlp_grad(const float *feats, const float *target, int n, const float *weights, float *grad_out,
                             float *loss_out, void *stream);
 
+/* Diagnostic: y[i] = log(x[i]) evaluated by the library's double-float
+ * logarithm (the one the mixed form uses for the entropy functional); x, y
+ * device arrays of n float64 values, x > 0.  Synchronises the stream. */
+perrk_status perrk_df_log(const double *x, double *y, int n, void *stream);
+
 /* Last CUDA error string seen by this thread (static storage). */
 const char *perrk_last_error(void);
 const char *perrk_status_string(perrk_status s);

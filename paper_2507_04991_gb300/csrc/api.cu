@@ -56,7 +56,8 @@ static perrk_status upload(T *&dst, const std::vector<T> &src, const char *what)
 static void free_ctx(Ctx &c) {
     void *ptrs[] = {c.U, c.K1, c.Ka, c.Kb, c.d, c.e_dh, c.g_node, c.g_elem, c.g_fnorm, c.g_wJ, c.g_nbr, c.g_gp,
                     c.g_elist, c.g_chunk_inst, c.g_chunk_e0, c.g_chunk_e1, c.g_inst_chunk0, c.g_inst_nchunks,
-                    c.g_coef, c.g_coef_f, c.g_scal, c.g_partials, c.g_counters, c.g_flags, c.g_records, c.g_mlp};
+                    c.g_coef, c.g_coef_f, c.g_scal, c.g_partials, c.g_counters, c.g_flags, c.g_records, c.g_mlp,
+                    c.g_dftab};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c.graph_exec) cudaGraphExecDestroy((cudaGraphExec_t)c.graph_exec);
@@ -78,6 +79,10 @@ static perrk_status upload_coefficients(Ctx &c) {
 }
 
 static perrk_status alloc_ctx(Ctx &c) {
+    int dev = 0, sms = 152;
+    PERRK_CUDA(cudaGetDevice(&dev), "device query");
+    PERRK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "device query");
+    make_chunks(c, sms);
     const size_t nstate = (size_t)c.V * c.n_elem * c.NP;
     double **bufs[] = {&c.U, &c.K1, &c.Ka, &c.Kb, &c.d};
     for (double **b : bufs) {
@@ -117,6 +122,12 @@ static perrk_status alloc_ctx(Ctx &c) {
     PERRK_CUDA(cudaMemset(c.g_counters, 0, (size_t)c.n_inst * sizeof(uint32_t)), "counters clear");
     PERRK_CUDA(cudaMalloc((void **)&c.g_flags, sizeof(uint32_t)), "flags alloc");
     PERRK_CUDA(cudaMemset(c.g_flags, 0, sizeof(uint32_t)), "flags clear");
+    {
+        std::vector<float> tab, consts;
+        df_tables(c.gamma_gas, tab, consts);
+        PERRK_TRY(upload(c.g_dftab, tab, "df table"));
+        for (int i = 0; i < 8; ++i) c.df_consts[i] = consts[i];
+    }
     c.rec_cap = 256;
     PERRK_CUDA(cudaMalloc((void **)&c.g_records, (size_t)c.rec_cap * c.n_inst * sizeof(perrk_step_info)), "records");
     return upload_coefficients(c);
@@ -405,6 +416,20 @@ perrk_status perrk_mlp_grad(const float *feats, const float *target, int n, cons
     if (!feats || !target || !weights || !grad_out || n <= 0) return PERRK_INVALID_ARG;
     std::vector<float> w(weights, weights + perrk_mlp_size());
     return mlp_train_device(feats, target, n, w.data(), 0, 0.0f, loss_out, grad_out, stream);
+}
+
+perrk_status perrk_df_log(const double *x, double *y, int n, void *stream) {
+    if (!x || !y || n < 0) return PERRK_INVALID_ARG;
+    std::vector<float> tab, consts;
+    df_tables(1.4, tab, consts);
+    float *dtab = nullptr, *dk = nullptr;
+    PERRK_TRY(upload(dtab, tab, "df table"));
+    perrk_status s = upload(dk, consts, "df consts");
+    if (s == PERRK_OK) s = launch_df_log(dtab, dk, x, y, n, stream);
+    if (s == PERRK_OK) s = cuda_check((int)cudaStreamSynchronize((cudaStream_t)stream), "df_log sync");
+    cudaFree(dtab);
+    if (dk) cudaFree(dk);
+    return s;
 }
 
 const char *perrk_last_error(void) { return g_err.c_str(); }

@@ -1,0 +1,103 @@
+// Double-float ("df") arithmetic on the FP32 pipe: a value is hi + lo with two
+// floats, |lo| <= ulp(hi)/2, about 48 significant bits.  On GB300 the FP64
+// pipe issues at 1/70 of the FP32 rate, so the mixed form evaluates the
+// entropy functional (a log per node) in df instead of float64.
+//
+// Error-free transformations: TwoSum (Knuth), FastTwoSum (Dekker), TwoProd
+// via FMA.  Logarithm: table-driven reduction in the manner of Tang (1990,
+// "Table-driven implementation of the logarithm function in IEEE
+// floating-point arithmetic"): x = 2^k m, m in [1,2), F = 1 + j/128 nearest
+// to m, r = (m - F)/F with |r| <= 2^-8, log x = k log 2 + log F + log1p(r),
+// log1p(r) = r - r^2/2 + r^3/3 - ... with the first three terms in df and the
+// tail from r^4 on in float.  log F and 1/F come from a host-built table
+// (long double, split into float pairs).
+#pragma once
+
+#include <cstdint>
+
+namespace perrk {
+
+struct df {
+    float hi, lo;
+};
+
+struct DfConst {
+    df ln2, third, gm1, gam;   // log 2, 1/3, gamma - 1, gamma as float pairs
+};
+
+__device__ __forceinline__ df df_two_sum(float a, float b) {
+    const float s = a + b;
+    const float bb = s - a;
+    return df{s, (a - (s - bb)) + (b - bb)};
+}
+
+__device__ __forceinline__ df df_fast(float a, float b) {  // |a| >= |b|
+    const float s = a + b;
+    return df{s, b - (s - a)};
+}
+
+__device__ __forceinline__ df df_add(df x, df y) {
+    df s = df_two_sum(x.hi, y.hi);
+    df t = df_two_sum(x.lo, y.lo);
+    float e = s.lo + t.hi;
+    s = df_fast(s.hi, e);
+    e = s.lo + t.lo;
+    return df_fast(s.hi, e);
+}
+
+__device__ __forceinline__ df df_neg(df x) { return df{-x.hi, -x.lo}; }
+
+__device__ __forceinline__ df df_sub(df x, df y) { return df_add(x, df_neg(y)); }
+
+__device__ __forceinline__ df df_mul(df x, df y) {
+    const float p = x.hi * y.hi;
+    float e = fmaf(x.hi, y.hi, -p);
+    e = fmaf(x.hi, y.lo, e);
+    e = fmaf(x.lo, y.hi, e);
+    return df_fast(p, e);
+}
+
+__device__ __forceinline__ df df_mul_f(df x, float f) {
+    const float p = x.hi * f;
+    float e = fmaf(x.hi, f, -p);
+    e = fmaf(x.lo, f, e);
+    return df_fast(p, e);
+}
+
+__device__ __forceinline__ df df_div(df x, df y) {
+    const float q1 = __fdiv_rn(x.hi, y.hi);
+    const df r = df_sub(x, df_mul_f(y, q1));
+    const float q2 = __fdiv_rn(r.hi, y.hi);
+    return df_fast(q1, q2);
+}
+
+// float64 -> df (one FP64 subtraction) and back (one FP64 addition).
+__device__ __forceinline__ df df_from(double d) {
+    const float hi = __double2float_rn(d);
+    return df{hi, __double2float_rn(d - (double)hi)};
+}
+
+__device__ __forceinline__ double df_to(df x) { return (double)x.hi + (double)x.lo; }
+
+// log(x) for x > 0 (x.hi a normal float).  tab[j] = (log F_j hi, lo, 1/F_j hi, lo).
+__device__ __forceinline__ df df_log(df x, const float4 *__restrict__ tab, const DfConst &K) {
+    const uint32_t bits = __float_as_uint(x.hi);
+    const int k = (int)((bits >> 23) & 0xffu) - 127;
+    const float mh = __uint_as_float((bits & 0x7fffffu) | 0x3f800000u);   // hi / 2^k in [1, 2)
+    const float ml = x.lo * __uint_as_float((uint32_t)(127 - k) << 23);   // lo / 2^k
+    const int j = __float2int_rn((mh - 1.0f) * 128.0f);
+    const float F = 1.0f + (float)j * 0.0078125f;
+    const float4 t = __ldg(tab + j);
+    // r = (m - F) / F: m_hi - F is exact (Sterbenz), then times 1/F in df
+    const df d = df_two_sum(mh - F, ml);
+    const df r = df_mul(d, df{t.z, t.w});
+    const float rh = r.hi;
+    const float tail = fmaf(rh, fmaf(rh, fmaf(rh, 1.0f / 7.0f, -1.0f / 6.0f), 1.0f / 5.0f), -0.25f);
+    const df inner = df_add(K.third, df_mul_f(r, tail));             // 1/3 + r t
+    const df inner2 = df_add(df{-0.5f, 0.0f}, df_mul(r, inner));      // -1/2 + r (...)
+    const df l1p = df_add(r, df_mul(r, df_mul(r, inner2)));           // r + r^2 (...)
+    const df kl = df_mul_f(K.ln2, (float)k);
+    return df_add(df_add(kl, df{t.x, t.y}), l1p);
+}
+
+}  // namespace perrk

@@ -17,6 +17,7 @@
 
 #include <cmath>
 
+#include "dfloat.cuh"
 #include "physics.cuh"
 
 namespace perrk {
@@ -36,7 +37,52 @@ struct RelaxParams {
     double gamma_gas;
     int max_it, guess, target, relax, query;
     double tol_r, tol_g;
+    const float4 *dftab;    // double-float log table (mixed form)
+    DfConst K;
 };
+
+// Entropy of one node in double-float (mixed form): returns s and, when
+// dv != nullptr, the float value of <w(u), dv>.  s = -rho (log p - gamma log rho).
+template <int DIM, int EQ>
+__device__ __forceinline__ df df_entropy(const double *u, const double *dv, const RelaxParams &P, float &wd,
+                                         uint32_t &bad) {
+    constexpr int V = EQ == EQ_BURGERS ? 1 : DIM + 2;
+    if constexpr (EQ == EQ_BURGERS) {
+        const df x = df_from(u[0]);
+        df sq = df_mul(x, x);
+        if (dv) wd = x.hi * (float)dv[0];
+        return df{0.5f * sq.hi, 0.5f * sq.lo};
+    } else {
+        df x[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) x[v] = df_from(u[v]);
+        const df ir = df_div(df{1.0f, 0.0f}, x[0]);
+        df m2 = df_mul(x[1], x[1]);
+#pragma unroll
+        for (int a = 1; a < DIM; ++a) m2 = df_add(m2, df_mul(x[1 + a], x[1 + a]));
+        df ke = df_mul(m2, ir);
+        ke.hi *= 0.5f;
+        ke.lo *= 0.5f;
+        const df p = df_mul(P.K.gm1, df_sub(x[DIM + 1], ke));
+        if (!(x[0].hi > 0.0f) || !(p.hi > 0.0f) || !isfinite(p.hi)) {
+            bad |= PERRK_FLAG_NONPHYSICAL;
+            wd = 0.0f;
+            return df{0.0f, 0.0f};
+        }
+        const df lp = df_log(p, P.dftab, P.K), lr = df_log(x[0], P.dftab, P.K);
+        const df S = df_sub(lp, df_mul(P.K.gam, lr));
+        if (dv) {
+            // w in float: (gamma - S - (gamma-1) |m|^2/(2 rho p), (gamma-1) m/p, -(gamma-1) rho/p)
+            const float gm1 = P.K.gm1.hi, ip = 1.0f / p.hi;
+            const float w0 = P.K.gam.hi - S.hi - gm1 * ke.hi * ip;
+            float md = 0.0f;
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) md = fmaf(x[1 + a].hi, (float)dv[1 + a], md);
+            wd = fmaf(w0, (float)dv[0], gm1 * ip * (md - x[0].hi * (float)dv[DIM + 1]));
+        }
+        return df_neg(df_mul(x[0], S));
+    }
+}
 
 template <int DIM, int EQ>
 __device__ __forceinline__ void node_entropy(const double *u, double gam, double &s, double *w, uint32_t &bad) {
@@ -48,9 +94,10 @@ __device__ __forceinline__ void node_entropy(const double *u, double gam, double
     }
 }
 
-// Write this block's NQ compensated sums, take a ticket; returns true in
-// thread 0 of the instance's last block, whose sums over all chunks (in chunk
-// order) are then in tot[].
+// Write this block's NQ compensated sums and take a ticket.  The instance's
+// last block then reduces all chunk partials with all of its threads (fixed
+// strided assignment and fixed tree: deterministic); returns true in its
+// thread 0, where tot[] holds the instance totals.
 template <int NQ>
 __device__ __forceinline__ bool chunk_finish(const RelaxParams &P, int chunk, int inst, double (&s)[NQ], double (&c)[NQ],
                                              double (&tot)[NQ]) {
@@ -67,17 +114,22 @@ __device__ __forceinline__ bool chunk_finish(const RelaxParams &P, int chunk, in
         s_last = (ticket == (unsigned)P.inst_nchunks[inst] - 1u);
     }
     __syncthreads();
-    if (!s_last || threadIdx.x != 0) return false;
+    if (!s_last) return false;
     __threadfence();
     const int c0 = P.inst_chunk0[inst], nc = P.inst_nchunks[inst];
+    double ss[NQ], cc[NQ];
     for (int k = 0; k < NQ; ++k) {
-        double ss = 0.0, cc = 0.0;
-        for (int j = 0; j < nc; ++j) {
-            comp_add(ss, cc, __ldcg(P.partials + (size_t)(c0 + j) * 8 + 2 * k));
-            cc += __ldcg(P.partials + (size_t)(c0 + j) * 8 + 2 * k + 1);
-        }
-        tot[k] = ss + cc;
+        ss[k] = 0.0;
+        cc[k] = 0.0;
     }
+    for (int j = threadIdx.x; j < nc; j += blockDim.x)
+        for (int k = 0; k < NQ; ++k) {
+            comp_add(ss[k], cc[k], __ldcg(P.partials + (size_t)(c0 + j) * 8 + 2 * k));
+            cc[k] += __ldcg(P.partials + (size_t)(c0 + j) * 8 + 2 * k + 1);
+        }
+    block_sum<NQ>(ss, cc, sm);
+    if (threadIdx.x != 0) return false;
+    for (int k = 0; k < NQ; ++k) tot[k] = ss[k] + cc[k];
     P.counters[inst] = 0u;
     return true;
 }
@@ -129,7 +181,7 @@ __global__ void k_relax_init(const RelaxParams P) {
     }
 }
 
-template <int DIM, int EQ>
+template <int DIM, int EQ, bool DF>
 __global__ void __launch_bounds__(256) k_newton_pass(const RelaxParams P) {
     constexpr int NP = ipow4(DIM);
     constexpr int V = EQ == EQ_BURGERS ? 1 : DIM + 2;
@@ -141,21 +193,44 @@ __global__ void __launch_bounds__(256) k_newton_pass(const RelaxParams P) {
     const size_t n0 = (size_t)P.chunk_e0[chunk] * NP, n1 = (size_t)P.chunk_e1[chunk] * NP;
     double s[3] = {0, 0, 0}, c[3] = {0, 0, 0}, tot[3];
     uint32_t bad = 0;
-    for (size_t j = n0 + threadIdx.x; j < n1; j += blockDim.x) {
-        double u[V], dv[V], w[V], sv;
+    if constexpr (DF) {
+        df R = {0.0f, 0.0f};
+        float G = 0.0f, A = 0.0f;
+        for (size_t j = n0 + threadIdx.x; j < n1; j += blockDim.x) {
+            double u[V], dv[V];
 #pragma unroll
-        for (int v = 0; v < V; ++v) {
-            dv[v] = __ldg(P.d + v * NPtot + j);
-            u[v] = fma(gdt, dv[v], __ldg(P.U + v * NPtot + j));
+            for (int v = 0; v < V; ++v) {
+                dv[v] = __ldg(P.d + v * NPtot + j);
+                u[v] = fma(gdt, dv[v], __ldg(P.U + v * NPtot + j));
+            }
+            float wd;
+            const df sv = df_entropy<DIM, EQ>(u, dv, P, wd, bad);
+            const df wj = df_from(__ldg(P.wJ + j));
+            R = df_add(R, df_mul(sv, wj));
+            G = fmaf(wj.hi, wd, G);
+            A = fmaf(wj.hi, fabsf(sv.hi), A);
         }
-        node_entropy<DIM, EQ>(u, P.gamma_gas, sv, w, bad);
-        double wd = 0.0;
+        s[0] = (double)R.hi;
+        c[0] = (double)R.lo;
+        s[1] = (double)G * dt;
+        s[2] = (double)A;
+    } else {
+        for (size_t j = n0 + threadIdx.x; j < n1; j += blockDim.x) {
+            double u[V], dv[V], w[V], sv;
 #pragma unroll
-        for (int v = 0; v < V; ++v) wd = fma(w[v], dv[v], wd);
-        const double wj = __ldg(P.wJ + j);
-        comp_add(s[0], c[0], wj * sv);
-        comp_add(s[1], c[1], wj * dt * wd);
-        comp_add(s[2], c[2], wj * fabs(sv));
+            for (int v = 0; v < V; ++v) {
+                dv[v] = __ldg(P.d + v * NPtot + j);
+                u[v] = fma(gdt, dv[v], __ldg(P.U + v * NPtot + j));
+            }
+            node_entropy<DIM, EQ>(u, P.gamma_gas, sv, w, bad);
+            double wd = 0.0;
+#pragma unroll
+            for (int v = 0; v < V; ++v) wd = fma(w[v], dv[v], wd);
+            const double wj = __ldg(P.wJ + j);
+            comp_add(s[0], c[0], wj * sv);
+            comp_add(s[1], c[1], wj * dt * wd);
+            comp_add(s[2], c[2], wj * fabs(sv));
+        }
     }
     if (bad) atomicOr(P.flags, bad);
     if (!chunk_finish<3>(P, chunk, inst, s, c, tot)) return;
@@ -197,7 +272,7 @@ __global__ void __launch_bounds__(256) k_newton_pass(const RelaxParams P) {
     if (S.done) accept_gamma(S);
 }
 
-template <int DIM, int EQ>
+template <int DIM, int EQ, bool DF>
 __global__ void __launch_bounds__(256) k_update(const RelaxParams P) {
     constexpr int NP = ipow4(DIM);
     constexpr int V = EQ == EQ_BURGERS ? 1 : DIM + 2;
@@ -218,11 +293,19 @@ __global__ void __launch_bounds__(256) k_update(const RelaxParams P) {
             if (!isfinite(u[v])) bad |= PERRK_FLAG_NONFINITE;
         }
         if (needH) {
-            double sv;
-            node_entropy<DIM, EQ>(u, P.gamma_gas, sv, nullptr, bad);
-            const double wj = __ldg(P.wJ + j);
-            comp_add(s[0], c[0], wj * sv);
-            comp_add(s[1], c[1], wj * fabs(sv));
+            if constexpr (DF) {
+                float wd;
+                const df sv = df_entropy<DIM, EQ>(u, nullptr, P, wd, bad);
+                const double t = df_to(df_mul(sv, df_from(__ldg(P.wJ + j))));
+                comp_add(s[0], c[0], t);
+                comp_add(s[1], c[1], fabs(t));
+            } else {
+                double sv;
+                node_entropy<DIM, EQ>(u, P.gamma_gas, sv, nullptr, bad);
+                const double wj = __ldg(P.wJ + j);
+                comp_add(s[0], c[0], wj * sv);
+                comp_add(s[1], c[1], wj * fabs(sv));
+            }
         }
     }
     if (bad) atomicOr(P.flags, bad);
@@ -267,7 +350,7 @@ __global__ void __launch_bounds__(256) k_update(const RelaxParams P) {
     S.nsteps_done += 1;
 }
 
-template <int DIM, int EQ>
+template <int DIM, int EQ, bool DF>
 __global__ void __launch_bounds__(256) k_entropy(const RelaxParams P) {
     constexpr int NP = ipow4(DIM);
     constexpr int V = EQ == EQ_BURGERS ? 1 : DIM + 2;
@@ -278,13 +361,22 @@ __global__ void __launch_bounds__(256) k_entropy(const RelaxParams P) {
     double s[2] = {0, 0}, c[2] = {0, 0}, tot[2];
     uint32_t bad = 0;
     for (size_t j = n0 + threadIdx.x; j < n1; j += blockDim.x) {
-        double u[V], sv;
+        double u[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) u[v] = __ldg(P.U + v * NPtot + j);
-        node_entropy<DIM, EQ>(u, P.gamma_gas, sv, nullptr, bad);
-        const double wj = __ldg(P.wJ + j);
-        comp_add(s[0], c[0], wj * sv);
-        comp_add(s[1], c[1], wj * fabs(sv));
+        if constexpr (DF) {
+            float wd;
+            const df sv = df_entropy<DIM, EQ>(u, nullptr, P, wd, bad);
+            const double t = df_to(df_mul(sv, df_from(__ldg(P.wJ + j))));
+            comp_add(s[0], c[0], t);
+            comp_add(s[1], c[1], fabs(t));
+        } else {
+            double sv;
+            node_entropy<DIM, EQ>(u, P.gamma_gas, sv, nullptr, bad);
+            const double wj = __ldg(P.wJ + j);
+            comp_add(s[0], c[0], wj * sv);
+            comp_add(s[1], c[1], wj * fabs(sv));
+        }
     }
     if (bad) atomicOr(P.flags, bad);
     if (!chunk_finish<2>(P, chunk, inst, s, c, tot)) return;
@@ -333,22 +425,54 @@ static RelaxParams relax_params(Ctx &c) {
     P.relax = c.opt.relaxation;
     P.tol_r = c.opt.newton_tol_r;
     P.tol_g = c.opt.newton_tol_g;
+    P.dftab = (const float4 *)c.g_dftab;
+    P.K.ln2 = df{c.df_consts[0], c.df_consts[1]};
+    P.K.third = df{c.df_consts[2], c.df_consts[3]};
+    P.K.gm1 = df{c.df_consts[4], c.df_consts[5]};
+    P.K.gam = df{c.df_consts[6], c.df_consts[7]};
     return P;
 }
 
-#define PERRK_RELAX_DISPATCH(NAME, KERNEL)                                                       \
-    static void NAME(Ctx &c, const RelaxParams &P, cudaStream_t st, int threads) {              \
-        const int nb = (int)c.chunk_inst.size();                                                 \
-        if (c.equation == PERRK_BURGERS_1D) KERNEL<1, EQ_BURGERS><<<nb, threads, 0, st>>>(P);   \
-        else if (c.dim == 1) KERNEL<1, EQ_EULER><<<nb, threads, 0, st>>>(P);                    \
-        else if (c.dim == 2) KERNEL<2, EQ_EULER><<<nb, threads, 0, st>>>(P);                    \
-        else KERNEL<3, EQ_EULER><<<nb, threads, 0, st>>>(P);                                    \
+#define PERRK_RELAX_DISPATCH(NAME, KERNEL, TPL)                                                  \
+    static void NAME(Ctx &c, const RelaxParams &P, cudaStream_t st, int threads) {                 \
+        const int nb = (int)c.chunk_inst.size();                                                    \
+        const bool df = c.opt.precision == PERRK_MIXED;                                             \
+        if (c.equation == PERRK_BURGERS_1D) {                                                       \
+            if (df) KERNEL<1, EQ_BURGERS TPL(true)><<<nb, threads, 0, st>>>(P);                    \
+            else KERNEL<1, EQ_BURGERS TPL(false)><<<nb, threads, 0, st>>>(P);                      \
+        } else if (c.dim == 1) {                                                                    \
+            if (df) KERNEL<1, EQ_EULER TPL(true)><<<nb, threads, 0, st>>>(P);                      \
+            else KERNEL<1, EQ_EULER TPL(false)><<<nb, threads, 0, st>>>(P);                        \
+        } else if (c.dim == 2) {                                                                    \
+            if (df) KERNEL<2, EQ_EULER TPL(true)><<<nb, threads, 0, st>>>(P);                      \
+            else KERNEL<2, EQ_EULER TPL(false)><<<nb, threads, 0, st>>>(P);                        \
+        } else {                                                                                    \
+            if (df) KERNEL<3, EQ_EULER TPL(true)><<<nb, threads, 0, st>>>(P);                      \
+            else KERNEL<3, EQ_EULER TPL(false)><<<nb, threads, 0, st>>>(P);                        \
+        }                                                                                           \
     }
-PERRK_RELAX_DISPATCH(run_init, k_relax_init)
-PERRK_RELAX_DISPATCH(run_pass, k_newton_pass)
-PERRK_RELAX_DISPATCH(run_update, k_update)
-PERRK_RELAX_DISPATCH(run_entropy, k_entropy)
+#define PERRK_WITH_DF(x) , x
+#define PERRK_NO_DF(x)
+PERRK_RELAX_DISPATCH(run_init, k_relax_init, PERRK_NO_DF)
+PERRK_RELAX_DISPATCH(run_pass, k_newton_pass, PERRK_WITH_DF)
+PERRK_RELAX_DISPATCH(run_update, k_update, PERRK_WITH_DF)
+PERRK_RELAX_DISPATCH(run_entropy, k_entropy, PERRK_WITH_DF)
 #undef PERRK_RELAX_DISPATCH
+
+__global__ void k_df_log(const float4 *tab, const float *kc, const double *x, double *y, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    DfConst K;
+    K.ln2 = df{kc[0], kc[1]};
+    K.third = df{kc[2], kc[3]};
+    y[i] = df_to(df_log(df_from(x[i]), tab, K));
+}
+
+perrk_status launch_df_log(const float *tab, const float *consts, const double *x, double *y, int n, void *stream) {
+    if (n == 0) return PERRK_OK;
+    k_df_log<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>((const float4 *)tab, consts, x, y, n);
+    return cuda_check((int)cudaGetLastError(), "df_log launch");
+}
 
 perrk_status launch_relax_init(Ctx &c, void *stream) {
     RelaxParams P = relax_params(c);

@@ -119,12 +119,14 @@ struct Ctx {
     perrk_step_info *g_records = nullptr;     // [rec_cap][n_inst]
     int rec_cap = 0;
     float *g_mlp = nullptr;                   // weights (nullptr: no MLP)
+    float *g_dftab = nullptr;                 // double-float log table [129][4]
+    float df_consts[8] = {0};                 // log 2, 1/3, gamma-1, gamma (float pairs)
     int mlp_on = 0;
 
     // launch configuration (autotuned)
     int stage_epb = 0;                        // elements per CTA in the stage kernel
     int stage_persistent = 0;                 // grid = min(groups, persistent blocks)
-    int relax_threads = 256;
+    int relax_threads = 128;
     bool tuned = false;
 
     // CUDA graph of one step
@@ -138,6 +140,8 @@ void lgl_tables(std::vector<double> &x, std::vector<double> &w, std::vector<doub
 perrk_status build_ctx(Ctx &c, int n, const perrk_mesh_desc *mesh, const perrk_scheme_desc *scheme,
                        const perrk_options *opts, std::string &err);
 void stage_coefficients(const Ctx &c, std::vector<StageCoef> &coef, std::vector<StageCoefF> &coef_f);
+void make_chunks(Ctx &c, int sm_count);
+void df_tables(double gamma_gas, std::vector<float> &tab, std::vector<float> &consts);
 
 // device side (kernels_*.cu)
 perrk_status launch_stage(Ctx &c, int stage, const double *U, double *Kout, const double *Kprev,
@@ -148,6 +152,7 @@ perrk_status launch_update(Ctx &c, int rec_slot, void *stream);
 perrk_status launch_entropy_set(Ctx &c, void *stream);
 perrk_status launch_entropy(Ctx &c, int query, void *stream);
 perrk_status launch_mlp_guess(Ctx &c, void *stream);
+perrk_status launch_df_log(const float *tab, const float *consts, const double *x, double *y, int n, void *stream);
 perrk_status mlp_train_device(const float *feats, const float *target, int n, float *weights, int epochs,
                               float lr, float *loss, float *grad_out, void *stream);
 

@@ -373,12 +373,23 @@ perrk_status build_ctx(Ctx &c, int n, const perrk_mesh_desc *mesh, const perrk_s
         for (int j = 0; j < I.S; ++j)
             if (I.b[j] != 0.0) c.any_b[j == 0 ? 0 : S - I.S + j] = 1;
     }
-    // relaxation work chunks (contiguous element ranges inside one instance)
-    c.chunk_elems = std::max(1, 4096 / NP);
+    make_chunks(c, 152);
+    return PERRK_OK;
+}
+
+// Relaxation work chunks: contiguous element ranges inside one instance, sized
+// so that a pass has at least ~4 blocks per SM (nodes per chunk between 128
+// and 4096).
+void make_chunks(Ctx &c, int sm_count) {
+    const int NP = c.NP;
+    const long long nodes = (long long)c.n_elem * NP;
+    long long target = nodes / (4LL * std::max(1, sm_count));
+    target = std::max(128LL, std::min(4096LL, target));
+    c.chunk_elems = std::max(1, (int)(target / NP));
     c.chunk_inst.clear();
     c.chunk_e0.clear();
     c.chunk_e1.clear();
-    for (int k = 0; k < n; ++k) {
+    for (int k = 0; k < c.n_inst; ++k) {
         Instance &I = c.inst[k];
         I.chunk0 = (int)c.chunk_inst.size();
         for (int e = 0; e < I.n_elem; e += c.chunk_elems) {
@@ -388,7 +399,6 @@ perrk_status build_ctx(Ctx &c, int n, const perrk_mesh_desc *mesh, const perrk_s
         }
         I.n_chunks = (int)c.chunk_inst.size() - I.chunk0;
     }
-    return PERRK_OK;
 }
 
 void stage_coefficients(const Ctx &c, std::vector<StageCoef> &coef, std::vector<StageCoefF> &coef_f) {
@@ -415,6 +425,28 @@ void stage_coefficients(const Ctx &c, std::vector<StageCoef> &coef, std::vector<
             }
         }
     }
+}
+
+// Tables of the double-float logarithm: for F_j = 1 + j/128 (j = 0..128)
+// log F_j and 1/F_j in long double, each split into a float pair; constants
+// log 2, 1/3, gamma - 1 and gamma as float pairs.
+static void split2(long double v, float &hi, float &lo) {
+    hi = (float)v;
+    lo = (float)(v - (long double)hi);
+}
+
+void df_tables(double gamma_gas, std::vector<float> &tab, std::vector<float> &consts) {
+    tab.assign(129 * 4, 0.0f);
+    for (int j = 0; j <= 128; ++j) {
+        const long double F = 1.0L + j / 128.0L;
+        split2(std::log(F), tab[4 * j + 0], tab[4 * j + 1]);
+        split2(1.0L / F, tab[4 * j + 2], tab[4 * j + 3]);
+    }
+    consts.assign(8, 0.0f);
+    split2(std::log(2.0L), consts[0], consts[1]);
+    split2(1.0L / 3.0L, consts[2], consts[3]);
+    split2((long double)gamma_gas - 1.0L, consts[4], consts[5]);
+    split2((long double)gamma_gas, consts[6], consts[7]);
 }
 
 }  // namespace perrk

@@ -295,7 +295,7 @@ __global__ void __launch_bounds__(EPB * ipow4(DIM)) k_stage(const StageParams P)
         double Kd[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-            Kd[v] = -(double)acc[v] * (double)invJ;
+            Kd[v] = (double)(-acc[v] * invJ);
             if (!isfinite(Kd[v])) bad |= PERRK_FLAG_NONFINITE;
             if (valid) P.Kout[v * NPtot + idx] = Kd[v];
         }
@@ -305,17 +305,46 @@ __global__ void __launch_bounds__(EPB * ipow4(DIM)) k_stage(const StageParams P)
             const StageCoef c = P.coef[g];
             double wdot = 0.0;
             if (c.b != 0.0) {
-                double Ui[V];
+                if constexpr (sizeof(Real) == 8) {
+                    double Ui[V];
 #pragma unroll
-                for (int v = 0; v < V; ++v) Ui[v] = P.stage1 ? Ud[v] : fma(c.asub, Kpd[v], fma(c.a1, K1d[v], Ud[v]));
-                if constexpr (EQ == EQ_BURGERS) {
-                    wdot = Ui[0] * Kd[0];
+                    for (int v = 0; v < V; ++v) Ui[v] = P.stage1 ? Ud[v] : fma(c.asub, Kpd[v], fma(c.a1, K1d[v], Ud[v]));
+                    if constexpr (EQ == EQ_BURGERS) {
+                        wdot = Ui[0] * Kd[0];
+                    } else {
+                        constexpr int DD = EQ == EQ_EULER ? DIM : 1;
+                        double s, w[DD + 2];
+                        euler_entropy<DD>(Ui, P.gamma_gas, s, w, bad);
+#pragma unroll
+                        for (int v = 0; v < V; ++v) wdot = fma(w[v], Kd[v], wdot);
+                    }
                 } else {
-                    constexpr int DD = EQ == EQ_EULER ? DIM : 1;
-                    double s, w[DD + 2];
-                    euler_entropy<DD>(Ui, P.gamma_gas, s, w, bad);
+                    // Mixed form: K_i carries FP32 rounding, so the integrand
+                    // <w(U_{n,i}), K_i> is evaluated from the FP32 stage state
+                    // and primitives (log p = log rho - log beta: no extra
+                    // logs); the per-element and global sums stay float64.
+                    Real wdf = 0;
+                    if constexpr (EQ == EQ_BURGERS) {
+                        wdf = u[0] * (-acc[0] * invJ);
+                    } else {
+                        constexpr int DD = EQ == EQ_EULER ? DIM : 1;
+                        const Real rho = s_pr[el][0][q], p = s_pr[el][DD + 1][q];
+                        const Real lr = s_pr[el][DD + 3][q], lb = s_pr[el][DD + 4][q];
+                        const Real S = (Real(1) - gam) * lr - lb;        // log p - gamma log rho
+                        const Real ip = rcp(p);
+                        Real v2 = 0, mk = 0;
 #pragma unroll
-                    for (int v = 0; v < V; ++v) wdot = fma(w[v], Kd[v], wdot);
+                        for (int a = 0; a < DD; ++a) {
+                            const Real va = s_pr[el][1 + a][q];
+                            v2 = dfma(va, va, v2);
+                            mk = dfma(va, -acc[1 + a] * invJ, mk);
+                        }
+                        const Real k0 = -acc[0] * invJ, kE = -acc[DD + 1] * invJ;
+                        const Real w0 = gam - S - gm1 * Real(0.5) * rho * v2 * ip;
+                        // w_m . K_m + w_E K_E = (gamma-1) rho / p (v . K_m - K_E)
+                        wdf = dfma(w0, k0, gm1 * rho * ip * (mk - kE));
+                    }
+                    wdot = (double)wdf;
                 }
                 wdot *= __ldg(P.wJ + idx);
                 if (valid) {

@@ -1,0 +1,45 @@
+"""GPU checks of building blocks: the double-float logarithm of the mixed
+form against CUDA's float64 log (error bound 2^-46), and the relaxation
+kernels' determinism."""
+import numpy as np
+import pytest
+
+import paper_2507_04991_gb300 as pk
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    import __graft_entry__
+    assert torch.cuda.is_available()
+    __graft_entry__.build()
+
+
+def test_df_log_against_cuda_log():
+    import torch
+    rng = np.random.default_rng(3)
+    x = np.concatenate([np.exp(rng.uniform(-30, 30, 200000)), 1 + rng.uniform(-1e-4, 1e-4, 50000),
+                        rng.uniform(0.2, 5.0, 200000), [1.0, 2.0, 0.5, 1.0 + 2.0 ** -20]])
+    xd = torch.tensor(x, device="cuda", dtype=torch.float64)
+    yd = torch.empty_like(xd)
+    pk.perrk_df_log(xd.data_ptr(), yd.data_ptr(), xd.numel())
+    ref = torch.log(xd)
+    err = (yd - ref).abs()
+    small = ref.abs() < 1
+    assert float(err[small].max()) < 2.0 ** -46                 # absolute, |log x| < 1
+    assert float((err[~small] / ref[~small].abs()).max()) < 2.0 ** -46
+    assert float(yd[-4]) == 0.0
+
+
+def test_repeatable_bitwise():
+    wl = workloads.small_box_2d(n=8, seed=41, R=2, E=[6, 3], order=3)
+    outs = []
+    for _ in range(2):
+        s = pk.Solver(wl, pk.options(precision=pk.MIXED))
+        recs = s.step(5)
+        outs.append((s.state(), [r[0]["gamma"] for r in recs]))
+        s.close()
+    assert np.array_equal(outs[0][0], outs[1][0]) and outs[0][1] == outs[1][1]
