@@ -54,7 +54,7 @@ static perrk_status upload(T *&dst, const std::vector<T> &src, const char *what)
 }
 
 static void free_ctx(Ctx &c) {
-    void *ptrs[] = {c.U, c.K1, c.Ka, c.Kb, c.d, c.e_dh, c.g_node, c.g_elem, c.g_fnorm, c.g_wJ, c.g_nbr, c.g_gp,
+    void *ptrs[] = {c.U, c.K1, c.Ka, c.Kb, c.d, c.Uf, c.K1f, c.Kaf, c.Kbf, c.e_dh, c.g_node, c.g_elem, c.g_fnorm, c.g_wJ, c.g_nbr, c.g_gp,
                     c.g_elist, c.g_chunk_inst, c.g_chunk_e0, c.g_chunk_e1, c.g_inst_chunk0, c.g_inst_nchunks,
                     c.g_coef, c.g_coef_f, c.g_scal, c.g_partials, c.g_counters, c.g_flags, c.g_records, c.g_mlp,
                     c.g_dftab};
@@ -84,10 +84,20 @@ static perrk_status alloc_ctx(Ctx &c) {
     PERRK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "device query");
     make_chunks(c, sms);
     const size_t nstate = (size_t)c.V * c.n_elem * c.NP;
-    double **bufs[] = {&c.U, &c.K1, &c.Ka, &c.Kb, &c.d};
-    for (double **b : bufs) {
+    const bool mixed = c.opt.precision == PERRK_MIXED;
+    // float64: U, K_1, two stage registers, d; mixed: float64 U and d, FP32 copy of
+    // U_n and FP32 stage registers (K is an FP32 result in that form)
+    std::vector<double **> dbufs = {&c.U, &c.d};
+    if (!mixed) dbufs.insert(dbufs.end(), {&c.K1, &c.Ka, &c.Kb});
+    for (double **b : dbufs) {
         PERRK_CUDA(cudaMalloc((void **)b, nstate * sizeof(double)), "state alloc");
         PERRK_CUDA(cudaMemset(*b, 0, nstate * sizeof(double)), "state clear");
+    }
+    if (mixed) {
+        for (float **b : {&c.Uf, &c.K1f, &c.Kaf, &c.Kbf}) {
+            PERRK_CUDA(cudaMalloc((void **)b, nstate * sizeof(float)), "state alloc");
+            PERRK_CUDA(cudaMemset(*b, 0, nstate * sizeof(float)), "state clear");
+        }
     }
     PERRK_CUDA(cudaMalloc((void **)&c.e_dh, (size_t)c.n_elem * sizeof(double)), "e_dh alloc");
     PERRK_CUDA(cudaMemset(c.e_dh, 0, (size_t)c.n_elem * sizeof(double)), "e_dh clear");
@@ -134,11 +144,7 @@ static perrk_status alloc_ctx(Ctx &c) {
 }
 
 static perrk_status enqueue_step(Ctx &c, cudaStream_t st) {
-    for (int i = 0; i < c.S; ++i) {
-        double *Kout = (i == 0) ? c.K1 : ((i % 2) ? c.Ka : c.Kb);
-        const double *Kprev = (i <= 1) ? c.K1 : (((i - 1) % 2) ? c.Ka : c.Kb);
-        PERRK_TRY(launch_stage(c, i, c.U, Kout, Kprev, false, st));
-    }
+    for (int i = 0; i < c.S; ++i) PERRK_TRY(launch_stage(c, i, false, nullptr, nullptr, nullptr, nullptr, st));
     PERRK_TRY(launch_relax_init(c, st));
     if (c.opt.relaxation) {
         if (c.opt.guess == PERRK_GUESS_MLP && c.mlp_on) PERRK_TRY(launch_mlp_guess(c, st));
@@ -222,6 +228,7 @@ perrk_status perrk_set_state(perrk_ctx *h, const double *u, int on_device, void 
     PERRK_CUDA(cudaMemcpyAsync(c.U, u, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st),
                "set_state copy");
     PERRK_CUDA(cudaMemsetAsync(c.g_flags, 0, sizeof(uint32_t), st), "flags clear");
+    if (c.Uf) PERRK_TRY(launch_convert(c.U, c.Uf, nullptr, nullptr, (size_t)c.V * c.n_elem * c.NP, st));
     PERRK_TRY(launch_entropy_set(c, st));
     h->host_steps = 0;
     if (!on_device) PERRK_CUDA(cudaStreamSynchronize(st), "set_state sync");
@@ -327,10 +334,7 @@ perrk_status perrk_entropy(perrk_ctx *h, double *H, void *stream) {
 
 perrk_status perrk_launch_stage(perrk_ctx *h, int stage, void *stream) {
     if (!h || stage < 0 || stage >= h->c.S) return PERRK_INVALID_ARG;
-    Ctx &c = h->c;
-    double *Kout = (stage == 0) ? c.K1 : ((stage % 2) ? c.Ka : c.Kb);
-    const double *Kprev = (stage <= 1) ? c.K1 : (((stage - 1) % 2) ? c.Ka : c.Kb);
-    return launch_stage(c, stage, c.U, Kout, Kprev, false, stream);
+    return launch_stage(h->c, stage, false, nullptr, nullptr, nullptr, nullptr, stream);
 }
 
 perrk_status perrk_stage_info(const perrk_ctx *h, int stage, int64_t *n_active, int64_t *bytes, int *n_stages,
@@ -338,7 +342,9 @@ perrk_status perrk_stage_info(const perrk_ctx *h, int stage, int64_t *n_active, 
     if (!h || stage < 0 || stage >= h->c.S) return PERRK_INVALID_ARG;
     const Ctx &c = h->c;
     const int NF = 2 * c.dim, NFP = ipow4(c.dim - 1);
-    const int64_t per_arr = (int64_t)c.V * c.NP * 8;  // one float64 state array, one element
+    const int64_t vals = (int64_t)c.V * c.NP;
+    const int64_t per_arr = vals * (c.opt.precision == PERRK_MIXED ? 4 : 8);  // U / K arrays, one element
+    const int64_t per_d = vals * 8;                                          // float64 direction
     std::vector<StageCoef> coef;
     std::vector<StageCoefF> coef_f;
     stage_coefficients(c, coef, coef_f);
@@ -350,10 +356,11 @@ perrk_status perrk_stage_info(const perrk_ctx *h, int stage, int64_t *n_active, 
         int64_t arrays = 1 /*U*/ + 1 /*K out*/;
         if (stage > 0) arrays += 1;               // K_1
         if (stage > 0 && sc.asub != 0.0) arrays += 1;  // K_{i-1}
-        if (sc.b != 0.0) arrays += (sc.first_b != 0.0) ? 1 : 2;  // d write (and read)
+        int64_t dbytes = 0;
+        if (sc.b != 0.0) dbytes = ((sc.first_b != 0.0) ? 1 : 2) * per_d;  // d write (and read)
         int64_t geo = c.curved ? (int64_t)c.NP * 5 * 8 + (int64_t)NF * NFP * 2 * 8 : (int64_t)(c.dim + 1 + NF) * 8;
         if (sc.b != 0.0) geo += (int64_t)c.NP * 8 + 8;  // omega J and the element's Delta H slot
-        tot += arrays * per_arr + geo + 4 * (2 + NF);  // element list, partition id, neighbours
+        tot += arrays * per_arr + dbytes + geo + 4 * (2 + NF);  // element list, partition id, neighbours
     }
     if (n_active) *n_active = na;
     if (bytes) *bytes = tot;
@@ -376,7 +383,13 @@ perrk_status perrk_stage_info(const perrk_ctx *h, int stage, int64_t *n_active, 
 
 perrk_status perrk_rhs(perrk_ctx *h, const double *u_in, double *k_out, void *stream) {
     if (!h || !u_in || !k_out) return PERRK_INVALID_ARG;
-    return launch_stage(h->c, 0, u_in, k_out, nullptr, true, stream);
+    Ctx &c = h->c;
+    if (c.opt.precision != PERRK_MIXED) return launch_stage(c, 0, true, u_in, nullptr, k_out, nullptr, stream);
+    // mixed form: FP32 input copy and FP32 result in the (transient) stage registers
+    const size_t n = (size_t)c.V * c.n_elem * c.NP;
+    PERRK_TRY(launch_convert(u_in, c.Kbf, nullptr, nullptr, n, stream));
+    PERRK_TRY(launch_stage(c, 0, true, nullptr, c.Kbf, nullptr, c.Kaf, stream));
+    return launch_convert(nullptr, nullptr, c.Kaf, k_out, n, stream);
 }
 
 int perrk_mlp_size(void) {

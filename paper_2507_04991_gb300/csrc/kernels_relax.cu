@@ -24,6 +24,7 @@ namespace perrk {
 
 struct RelaxParams {
     double *U;
+    float *Uf;             // mixed form: FP32 copy of the state, refreshed by the update
     const double *d, *e_dh, *wJ;
     const int32_t *chunk_inst, *chunk_e0, *chunk_e1, *inst_chunk0, *inst_nchunks;
     InstScalars *scal;
@@ -99,11 +100,52 @@ __device__ __forceinline__ void node_entropy(const double *u, double gam, double
 // strided assignment and fixed tree: deterministic); returns true in its
 // thread 0, where tot[] holds the instance totals.
 template <int NQ>
+__device__ __forceinline__ bool chunk_publish(const RelaxParams &P, int chunk, int inst, double (&s)[NQ],
+                                              double (&c)[NQ], double (&tot)[NQ]);
+
+template <int NQ>
 __device__ __forceinline__ bool chunk_finish(const RelaxParams &P, int chunk, int inst, double (&s)[NQ], double (&c)[NQ],
                                              double (&tot)[NQ]) {
+    __shared__ double sm0[2 * NQ * 32];
+    block_sum<NQ>(s, c, sm0);
+    return chunk_publish<NQ>(P, chunk, inst, s, c, tot);
+}
+
+// Block sum of a per-thread double-float value and two floats on the FP32
+// pipe (fixed shuffle tree); the block's result is valid in thread 0.
+__device__ __forceinline__ void block_sum_df(df &r, float &g, float &a) {
+    __shared__ float sm[4][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    for (int off = 16; off > 0; off >>= 1) {
+        df o{__shfl_down_sync(0xffffffffu, r.hi, off), __shfl_down_sync(0xffffffffu, r.lo, off)};
+        r = df_add(r, o);
+        g += __shfl_down_sync(0xffffffffu, g, off);
+        a += __shfl_down_sync(0xffffffffu, a, off);
+    }
+    if (lane == 0) {
+        sm[0][warp] = r.hi;
+        sm[1][warp] = r.lo;
+        sm[2][warp] = g;
+        sm[3][warp] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < nw; ++w) {
+            r = df_add(r, df{sm[0][w], sm[1][w]});
+            g += sm[2][w];
+            a += sm[3][w];
+        }
+    }
+    __syncthreads();
+}
+
+// Publish thread 0's block sums as the chunk's partial and take a ticket; the
+// instance's last block reduces all partials (see chunk_finish).
+template <int NQ>
+__device__ __forceinline__ bool chunk_publish(const RelaxParams &P, int chunk, int inst, double (&s)[NQ],
+                                              double (&c)[NQ], double (&tot)[NQ]) {
     __shared__ double sm[2 * NQ * 32];
     __shared__ int s_last;
-    block_sum<NQ>(s, c, sm);
     if (threadIdx.x == 0) {
         for (int k = 0; k < NQ; ++k) {
             P.partials[(size_t)chunk * 8 + 2 * k] = s[k];
@@ -210,10 +252,13 @@ __global__ void __launch_bounds__(256) k_newton_pass(const RelaxParams P) {
             G = fmaf(wj.hi, wd, G);
             A = fmaf(wj.hi, fabsf(sv.hi), A);
         }
+        block_sum_df(R, G, A);
         s[0] = (double)R.hi;
         c[0] = (double)R.lo;
         s[1] = (double)G * dt;
         s[2] = (double)A;
+        if (bad) atomicOr(P.flags, bad);
+        if (!chunk_publish<3>(P, chunk, inst, s, c, tot)) return;
     } else {
         for (size_t j = n0 + threadIdx.x; j < n1; j += blockDim.x) {
             double u[V], dv[V], w[V], sv;
@@ -231,9 +276,9 @@ __global__ void __launch_bounds__(256) k_newton_pass(const RelaxParams P) {
             comp_add(s[1], c[1], wj * dt * wd);
             comp_add(s[2], c[2], wj * fabs(sv));
         }
+        if (bad) atomicOr(P.flags, bad);
+        if (!chunk_finish<3>(P, chunk, inst, s, c, tot)) return;
     }
-    if (bad) atomicOr(P.flags, bad);
-    if (!chunk_finish<3>(P, chunk, inst, s, c, tot)) return;
     InstScalars &S = P.scal[inst];
     const double R = tot[0], G = tot[1], A = tot[2];
     double T, dT;
@@ -290,6 +335,7 @@ __global__ void __launch_bounds__(256) k_update(const RelaxParams P) {
         for (int v = 0; v < V; ++v) {
             u[v] = fma(gdt, __ldg(P.d + v * NPtot + j), P.U[v * NPtot + j]);
             P.U[v * NPtot + j] = u[v];
+            if constexpr (DF) P.Uf[v * NPtot + j] = __double2float_rn(u[v]);
             if (!isfinite(u[v])) bad |= PERRK_FLAG_NONFINITE;
         }
         if (needH) {
@@ -402,6 +448,7 @@ __global__ void __launch_bounds__(256) k_entropy(const RelaxParams P) {
 static RelaxParams relax_params(Ctx &c) {
     RelaxParams P{};
     P.U = c.U;
+    P.Uf = c.Uf;
     P.d = c.d;
     P.e_dh = c.e_dh;
     P.wJ = c.g_wJ;

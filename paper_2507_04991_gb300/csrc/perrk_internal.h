@@ -105,6 +105,7 @@ struct Ctx {
 
     // device buffers
     double *U = nullptr, *K1 = nullptr, *Ka = nullptr, *Kb = nullptr, *d = nullptr;
+    float *Uf = nullptr, *K1f = nullptr, *Kaf = nullptr, *Kbf = nullptr;   // mixed form
     double *e_dh = nullptr;                   // [n_elem] per-element b-weighted <w, K> sums
     double *g_node = nullptr, *g_elem = nullptr, *g_fnorm = nullptr, *g_wJ = nullptr;
     int32_t *g_nbr = nullptr, *g_gp = nullptr, *g_elist = nullptr;
@@ -144,8 +145,12 @@ void make_chunks(Ctx &c, int sm_count);
 void df_tables(double gamma_gas, std::vector<float> &tab, std::vector<float> &consts);
 
 // device side (kernels_*.cu)
-perrk_status launch_stage(Ctx &c, int stage, const double *U, double *Kout, const double *Kprev,
-                          bool rhs_only, void *stream);
+// One stage over its active prefix (rhs_only: F on all elements of the state
+// in_u / in_uf into out_k / out_kf instead of the step buffers).
+perrk_status launch_stage(Ctx &c, int stage, bool rhs_only, const double *in_u, const float *in_uf, double *out_k,
+                          float *out_kf, void *stream);
+perrk_status launch_convert(const double *src_d, float *dst_f, const float *src_f, double *dst_d, size_t n,
+                            void *stream);
 perrk_status launch_relax_init(Ctx &c, void *stream);
 perrk_status launch_newton_pass(Ctx &c, void *stream);
 perrk_status launch_update(Ctx &c, int rec_slot, void *stream);

@@ -21,8 +21,11 @@
 namespace perrk {
 
 struct StageParams {
-    const double *U, *K1, *Kprev;
-    double *Kout, *d, *e_dh;
+    const double *U, *K1, *Kprev;              // float64 form
+    double *Kout;
+    const float *Uf, *K1f, *Kprevf;            // mixed form: FP32 copy of U_n, FP32 stage registers
+    float *Koutf;
+    double *d, *e_dh;
     const int32_t *elist, *nbr, *gp;
     const StageCoef *coef;      // [n_gp] rows of this stage
     const StageCoefF *coef_f;
@@ -56,34 +59,44 @@ __device__ __forceinline__ int face_node_dev(int f, int kk) {
 }
 
 // Stage-row combination at one node; the same instruction sequence is used
-// for an element's own nodes and for its neighbours' face nodes.
+// for an element's own nodes and for its neighbours' face nodes.  The float64
+// form also returns the float64 inputs (for the entropy integrand).
 template <int V, typename Real>
 __device__ __forceinline__ void stage_state(const StageParams &P, size_t NPtot, size_t idx, int g, Real *u, double *Ud,
                                             double *K1d, double *Kpd) {
-    if (P.stage1) {
+    if constexpr (sizeof(Real) == 8) {
+        if (P.stage1) {
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                Ud[v] = __ldg(P.U + v * NPtot + idx);
+                K1d[v] = 0.0;
+                Kpd[v] = 0.0;
+                u[v] = (Real)Ud[v];
+            }
+            return;
+        }
+        const StageCoef c = P.coef[g];
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             Ud[v] = __ldg(P.U + v * NPtot + idx);
-            K1d[v] = 0.0;
-            Kpd[v] = 0.0;
-            u[v] = (Real)Ud[v];
+            K1d[v] = __ldg(P.K1 + v * NPtot + idx);
+            Kpd[v] = (c.asub != 0.0) ? __ldg(P.Kprev + v * NPtot + idx) : 0.0;
         }
-        return;
-    }
-    const StageCoef c = P.coef[g];
-#pragma unroll
-    for (int v = 0; v < V; ++v) {
-        Ud[v] = __ldg(P.U + v * NPtot + idx);
-        K1d[v] = __ldg(P.K1 + v * NPtot + idx);
-        Kpd[v] = (c.asub != 0.0) ? __ldg(P.Kprev + v * NPtot + idx) : 0.0;
-    }
-    if constexpr (sizeof(Real) == 8) {
 #pragma unroll
         for (int v = 0; v < V; ++v) u[v] = (Real)fma(c.asub, Kpd[v], fma(c.a1, K1d[v], Ud[v]));
     } else {
+        if (P.stage1) {
+#pragma unroll
+            for (int v = 0; v < V; ++v) u[v] = __ldg(P.Uf + v * NPtot + idx);
+            return;
+        }
         const StageCoefF cf = P.coef_f[g];
 #pragma unroll
-        for (int v = 0; v < V; ++v) u[v] = (Real)fmaf(cf.asub, (float)Kpd[v], fmaf(cf.a1, (float)K1d[v], (float)Ud[v]));
+        for (int v = 0; v < V; ++v) {
+            const float k1 = __ldg(P.K1f + v * NPtot + idx);
+            const float kp = (cf.asub != 0.0f) ? __ldg(P.Kprevf + v * NPtot + idx) : 0.0f;
+            u[v] = fmaf(cf.asub, kp, fmaf(cf.a1, k1, __ldg(P.Uf + v * NPtot + idx)));
+        }
     }
 }
 
@@ -292,12 +305,15 @@ __global__ void __launch_bounds__(EPB * ipow4(DIM)) k_stage(const StageParams P)
                 for (int v = 0; v < V; ++v) acc[v] += s_sf[el][sl][v];
             }
         }
-        double Kd[V];
+        Real Kr[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-            Kd[v] = (double)(-acc[v] * invJ);
-            if (!isfinite(Kd[v])) bad |= PERRK_FLAG_NONFINITE;
-            if (valid) P.Kout[v * NPtot + idx] = Kd[v];
+            Kr[v] = -acc[v] * invJ;
+            if (!isfinite(Kr[v])) bad |= PERRK_FLAG_NONFINITE;
+            if (valid) {
+                if constexpr (sizeof(Real) == 8) P.Kout[v * NPtot + idx] = Kr[v];
+                else P.Koutf[v * NPtot + idx] = Kr[v];
+            }
         }
 
         // ---- E: stages with b_i != 0: entropy integrand and direction
@@ -310,13 +326,13 @@ __global__ void __launch_bounds__(EPB * ipow4(DIM)) k_stage(const StageParams P)
 #pragma unroll
                     for (int v = 0; v < V; ++v) Ui[v] = P.stage1 ? Ud[v] : fma(c.asub, Kpd[v], fma(c.a1, K1d[v], Ud[v]));
                     if constexpr (EQ == EQ_BURGERS) {
-                        wdot = Ui[0] * Kd[0];
+                        wdot = Ui[0] * (double)Kr[0];
                     } else {
                         constexpr int DD = EQ == EQ_EULER ? DIM : 1;
                         double s, w[DD + 2];
                         euler_entropy<DD>(Ui, P.gamma_gas, s, w, bad);
 #pragma unroll
-                        for (int v = 0; v < V; ++v) wdot = fma(w[v], Kd[v], wdot);
+                        for (int v = 0; v < V; ++v) wdot = fma(w[v], (double)Kr[v], wdot);
                     }
                 } else {
                     // Mixed form: K_i carries FP32 rounding, so the integrand
@@ -325,7 +341,7 @@ __global__ void __launch_bounds__(EPB * ipow4(DIM)) k_stage(const StageParams P)
                     // logs); the per-element and global sums stay float64.
                     Real wdf = 0;
                     if constexpr (EQ == EQ_BURGERS) {
-                        wdf = u[0] * (-acc[0] * invJ);
+                        wdf = u[0] * Kr[0];
                     } else {
                         constexpr int DD = EQ == EQ_EULER ? DIM : 1;
                         const Real rho = s_pr[el][0][q], p = s_pr[el][DD + 1][q];
@@ -337,9 +353,9 @@ __global__ void __launch_bounds__(EPB * ipow4(DIM)) k_stage(const StageParams P)
                         for (int a = 0; a < DD; ++a) {
                             const Real va = s_pr[el][1 + a][q];
                             v2 = dfma(va, va, v2);
-                            mk = dfma(va, -acc[1 + a] * invJ, mk);
+                            mk = dfma(va, Kr[1 + a], mk);
                         }
-                        const Real k0 = -acc[0] * invJ, kE = -acc[DD + 1] * invJ;
+                        const Real k0 = Kr[0], kE = Kr[DD + 1];
                         const Real w0 = gam - S - gm1 * Real(0.5) * rho * v2 * ip;
                         // w_m . K_m + w_E K_E = (gamma-1) rho / p (v . K_m - K_E)
                         wdf = dfma(w0, k0, gm1 * rho * ip * (mk - kE));
@@ -351,7 +367,7 @@ __global__ void __launch_bounds__(EPB * ipow4(DIM)) k_stage(const StageParams P)
 #pragma unroll
                     for (int v = 0; v < V; ++v) {
                         double dold = (c.first_b != 0.0) ? 0.0 : P.d[v * NPtot + idx];
-                        P.d[v * NPtot + idx] = fma(c.b, Kd[v], dold);
+                        P.d[v * NPtot + idx] = fma(c.b, (double)Kr[v], dold);
                     }
                 }
             }

@@ -14,13 +14,36 @@ cudaError_t stage_launch_3d(const StageParams &, bool, bool, bool, int, int, cud
 
 int default_epb(int dim) { return dim == 1 ? 32 : (dim == 2 ? 8 : 2); }
 
-perrk_status launch_stage(Ctx &c, int stage, const double *U, double *Kout, const double *Kprev, bool rhs_only,
-                          void *stream) {
+__global__ void k_convert(const double *sd, float *df_, const float *sf, double *dd, size_t n) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (sd) df_[i] = __double2float_rn(sd[i]);
+    else dd[i] = (double)sf[i];
+}
+
+perrk_status launch_convert(const double *src_d, float *dst_f, const float *src_f, double *dst_d, size_t n,
+                            void *stream) {
+    if (n == 0) return PERRK_OK;
+    k_convert<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(src_d, dst_f, src_f, dst_d, n);
+    return cuda_check((int)cudaGetLastError(), "convert launch");
+}
+
+perrk_status launch_stage(Ctx &c, int stage, bool rhs_only, const double *in_u, const float *in_uf, double *out_k,
+                          float *out_kf, void *stream) {
     StageParams P{};
-    P.U = U;
+    const bool mixed = c.opt.precision == PERRK_MIXED;
+    P.U = rhs_only ? in_u : c.U;
+    P.Uf = rhs_only ? in_uf : c.Uf;
     P.K1 = c.K1;
-    P.Kprev = Kprev;
-    P.Kout = Kout;
+    P.K1f = c.K1f;
+    P.Kprev = (stage <= 1) ? c.K1 : (((stage - 1) % 2) ? c.Ka : c.Kb);
+    P.Kprevf = (stage <= 1) ? c.K1f : (((stage - 1) % 2) ? c.Kaf : c.Kbf);
+    P.Kout = rhs_only ? out_k : ((stage == 0) ? c.K1 : ((stage % 2) ? c.Ka : c.Kb));
+    P.Koutf = rhs_only ? out_kf : ((stage == 0) ? c.K1f : ((stage % 2) ? c.Kaf : c.Kbf));
+    if (mixed ? (!P.Uf || !P.Koutf) : (!P.U || !P.Kout)) {
+        set_error("stage buffers missing for the selected precision");
+        return PERRK_INVALID_ARG;
+    }
     P.d = c.d;
     P.e_dh = c.e_dh;
     P.elist = c.g_elist;
@@ -54,7 +77,7 @@ perrk_status launch_stage(Ctx &c, int stage, const double *U, double *Kout, cons
     const int groups = (P.n_active + epb - 1) / epb;
     int grid = groups;
     if (c.stage_persistent > 0) grid = std::min(groups, c.stage_persistent);
-    const bool burgers = c.equation == PERRK_BURGERS_1D, mixed = c.opt.precision == PERRK_MIXED;
+    const bool burgers = c.equation == PERRK_BURGERS_1D;
     cudaError_t e;
     if (c.dim == 1) e = stage_launch_1d(P, burgers, mixed, c.curved, epb, grid, (cudaStream_t)stream);
     else if (c.dim == 2) e = stage_launch_2d(P, burgers, mixed, c.curved, epb, grid, (cudaStream_t)stream);
