@@ -197,6 +197,10 @@ def run_native(args):
     plain_opts = pk.options(precision=pk.FP64, use_graph=True, max_it=args.max_it)
     chosen = pk.Solver(wl, chosen_opts)
     plain = pk.Solver(wl, plain_opts)
+    for sv in (chosen, plain):
+        pk.perrk_autotune(sv.h, stream=sh)
+        sv.set_state(wl.u0)
+    tuning = pk.perrk_tuning(chosen.h)
     info0 = pk.perrk_stage_info(chosen.h, 0)
     S = info0["n_stages"]
     dof_stage = info0["dof_stage_per_step"]
@@ -302,6 +306,7 @@ def run_native(args):
                    "form": "chosen: FP32 flux differencing and surface fluxes, float64 state, stage registers, "
                            "entropy reductions, Newton and update; one CUDA graph per step; Newton guess gamma_{n-1}",
                    "newton_max_it": args.max_it, "l2": "flushed (256 MiB write) before every timed step",
+                   "autotuned_mapping": tuning,
                    "parallelism": f"replicas x{world}"},
         "plain_fp64": {"value": plain_value, "ms_per_step": 1e3 * t_plain / max(1, args.steps // 2),
                        "stage_kernel_ms": k_ms_plain},

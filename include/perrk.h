@@ -174,6 +174,18 @@ perrk_status perrk_set_dt(perrk_ctx *ctx, int inst, double dt);
  * nsteps * n_inst records (step-major), which forces a stream sync. */
 perrk_status perrk_step(perrk_ctx *ctx, int nsteps, perrk_step_info *info, void *stream);
 
+/* Autotune the launch mapping of ctx on the current device: times the
+ * all-active stage kernel for every valid elements-per-CTA choice and grid
+ * mapping (one CTA per element group, or a persistent grid of k CTAs per SM)
+ * and the relaxation block size, keeps the fastest and re-captures the step
+ * graph.  Results do not depend on the mapping (same per-element
+ * arithmetic).  Overwrites K_1 (call between steps).  best_ms_out (nullable):
+ * time of the chosen stage launch.  Synchronises the stream. */
+perrk_status perrk_autotune(perrk_ctx *ctx, void *stream, float *best_ms_out);
+
+/* Current launch mapping (elements per CTA, persistent grid size or 0, relaxation block size). */
+perrk_status perrk_tuning(const perrk_ctx *ctx, int *elems_per_cta, int *persistent_grid, int *relax_threads);
+
 /* H(U) = sum omega J s(U) of the current state per instance (host array [n_inst]); syncs. */
 perrk_status perrk_entropy(perrk_ctx *ctx, double *H, void *stream);
 

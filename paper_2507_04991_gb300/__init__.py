@@ -32,7 +32,7 @@ EXPORTED = [
     "perrk_default_options", "perrk_create", "perrk_create_batched", "perrk_destroy", "perrk_build_tableau",
     "perrk_shape", "perrk_set_state", "perrk_get_state", "perrk_set_dt", "perrk_step", "perrk_entropy",
     "perrk_rhs", "perrk_mlp_size", "perrk_mlp_features", "perrk_set_mlp", "perrk_mlp_train", "perrk_mlp_grad",
-    "perrk_last_error", "perrk_status_string", "perrk_launch_stage", "perrk_stage_info", "perrk_df_log",
+    "perrk_last_error", "perrk_status_string", "perrk_launch_stage", "perrk_stage_info", "perrk_df_log", "perrk_autotune", "perrk_tuning",
 ]
 
 
@@ -98,6 +98,8 @@ def load(path=LIB_PATH):
         "perrk_last_error": (C.c_char_p, []),
         "perrk_launch_stage": (I, [P, I, P]),
         "perrk_df_log": (I, [P, P, I, P]),
+        "perrk_autotune": (I, [P, P, P]),
+        "perrk_tuning": (I, [P, P, P, P]),
         "perrk_stage_info": (I, [P, I, P, P, P, P, P]),
         "perrk_status_string": (C.c_char_p, [I]),
     }
@@ -287,6 +289,18 @@ def perrk_stage_info(h, stage):
            "perrk_stage_info")
     return dict(n_active=na.value, bytes=by.value, n_stages=ns.value, kernels_per_step=kps.value,
                 dof_stage_per_step=dsp.value)
+
+
+def perrk_autotune(h, stream=0):
+    ms = C.c_float(0.0)
+    _check(load().perrk_autotune(h, C.c_void_p(stream), C.byref(ms)), "perrk_autotune")
+    return ms.value
+
+
+def perrk_tuning(h):
+    a, b, c = C.c_int(), C.c_int(), C.c_int()
+    _check(load().perrk_tuning(h, C.byref(a), C.byref(b), C.byref(c)), "perrk_tuning")
+    return dict(elems_per_cta=a.value, persistent_grid=b.value, relax_threads=c.value)
 
 
 def perrk_df_log(x_ptr, y_ptr, n, stream=0):

@@ -57,7 +57,7 @@ static void free_ctx(Ctx &c) {
     void *ptrs[] = {c.U, c.K1, c.Ka, c.Kb, c.d, c.Uf, c.K1f, c.Kaf, c.Kbf, c.e_dh, c.g_node, c.g_elem, c.g_fnorm, c.g_wJ, c.g_nbr, c.g_gp,
                     c.g_elist, c.g_chunk_inst, c.g_chunk_e0, c.g_chunk_e1, c.g_inst_chunk0, c.g_inst_nchunks,
                     c.g_coef, c.g_coef_f, c.g_scal, c.g_partials, c.g_counters, c.g_flags, c.g_records, c.g_mlp,
-                    c.g_dftab};
+                    c.g_dftab, c.g_node_f, c.g_elem_f, c.g_fnorm_f, c.g_wJ_f};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c.graph_exec) cudaGraphExecDestroy((cudaGraphExec_t)c.graph_exec);
@@ -105,6 +105,13 @@ static perrk_status alloc_ctx(Ctx &c) {
     PERRK_TRY(upload(c.g_elem, c.geo_elem, "geometry"));
     PERRK_TRY(upload(c.g_fnorm, c.fnorm, "normals"));
     PERRK_TRY(upload(c.g_wJ, c.wJ, "weights"));
+    if (mixed) {
+        auto tof = [](const std::vector<double> &v) { return std::vector<float>(v.begin(), v.end()); };
+        PERRK_TRY(upload(c.g_node_f, tof(c.geo_node), "geometry"));
+        PERRK_TRY(upload(c.g_elem_f, tof(c.geo_elem), "geometry"));
+        PERRK_TRY(upload(c.g_fnorm_f, tof(c.fnorm), "normals"));
+        PERRK_TRY(upload(c.g_wJ_f, tof(c.wJ), "weights"));
+    }
     PERRK_TRY(upload(c.g_nbr, c.nbr, "neighbours"));
     PERRK_TRY(upload(c.g_gp, c.gp_of_elem, "partitions"));
     PERRK_TRY(upload(c.g_elist, c.elist, "element list"));
@@ -316,6 +323,84 @@ perrk_status perrk_step(perrk_ctx *h, int nsteps, perrk_step_info *info, void *s
             return PERRK_NONPHYSICAL_STATE;
         }
     }
+    return PERRK_OK;
+}
+
+perrk_status perrk_autotune(perrk_ctx *h, void *stream, float *best_ms_out) {
+    if (!h) return PERRK_INVALID_ARG;
+    Ctx &c = h->c;
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0, sms = 152;
+    PERRK_CUDA(cudaGetDevice(&dev), "device query");
+    PERRK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "device query");
+    std::vector<int> epbs = c.dim == 1 ? std::vector<int>{16, 32} : (c.dim == 2 ? std::vector<int>{4, 8, 16}
+                                                                              : std::vector<int>{1, 2, 4});
+    std::vector<int> grids = {0, 2 * sms, 4 * sms, 8 * sms};
+    cudaEvent_t e0, e1;
+    PERRK_CUDA(cudaEventCreate(&e0), "event");
+    PERRK_CUDA(cudaEventCreate(&e1), "event");
+    float best = 1e30f;
+    int best_epb = c.stage_epb, best_grid = c.stage_persistent;
+    const int save_epb = c.stage_epb, save_grid = c.stage_persistent;
+    for (int epb : epbs)
+        for (int g : grids) {
+            c.stage_epb = epb;
+            c.stage_persistent = g;
+            // warm-up launch; an unsupported configuration reports an error and is skipped
+            if (launch_stage(c, 0, false, nullptr, nullptr, nullptr, nullptr, st) != PERRK_OK) {
+                cudaGetLastError();
+                continue;
+            }
+            float tot = 0.0f;
+            bool ok = true;
+            for (int rep = 0; rep < 3 && ok; ++rep) {
+                cudaEventRecord(e0, st);
+                ok = launch_stage(c, 0, false, nullptr, nullptr, nullptr, nullptr, st) == PERRK_OK;
+                cudaEventRecord(e1, st);
+                cudaEventSynchronize(e1);
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                tot += ms;
+            }
+            if (ok && tot < best) {
+                best = tot;
+                best_epb = epb;
+                best_grid = g;
+            }
+        }
+    c.stage_epb = best < 1e29f ? best_epb : save_epb;
+    c.stage_persistent = best < 1e29f ? best_grid : save_grid;
+    // relaxation block size: time the entropy pass (a full-state float64/double-float pass)
+    float best_r = 1e30f;
+    int best_t = c.relax_threads;
+    for (int t : {128, 256}) {
+        c.relax_threads = t;
+        PERRK_TRY(launch_entropy(c, 1, st));
+        cudaEventRecord(e0, st);
+        PERRK_TRY(launch_entropy(c, 1, st));
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_r) {
+            best_r = ms;
+            best_t = t;
+        }
+    }
+    c.relax_threads = best_t;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c.tuned = true;
+    c.graph_dirty = true;
+    if (best_ms_out) *best_ms_out = best / 3.0f;
+    return cuda_check((int)cudaStreamSynchronize(st), "autotune sync");
+}
+
+perrk_status perrk_tuning(const perrk_ctx *h, int *elems_per_cta, int *persistent_grid, int *relax_threads) {
+    if (!h) return PERRK_INVALID_ARG;
+    if (elems_per_cta) *elems_per_cta = h->c.stage_epb;
+    if (persistent_grid) *persistent_grid = h->c.stage_persistent;
+    if (relax_threads) *relax_threads = h->c.relax_threads;
     return PERRK_OK;
 }
 

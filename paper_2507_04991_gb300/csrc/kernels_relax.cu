@@ -36,7 +36,7 @@ struct RelaxParams {
     int rec_slot, rec_cap, n_inst;
     size_t NE;
     double gamma_gas;
-    int max_it, guess, target, relax, query;
+    int max_it, guess, target, relax, query, mixed;
     double tol_r, tol_g;
     const float4 *dftab;    // double-float log table (mixed form)
     DfConst K;
@@ -193,13 +193,22 @@ __device__ void accept_gamma(InstScalars &s) {
 
 template <int DIM, int EQ>
 __global__ void k_relax_init(const RelaxParams P) {
-    constexpr int NP = ipow4(DIM);
     const int chunk = blockIdx.x;
     const int inst = P.chunk_inst[chunk];
     double s[1] = {0.0}, c[1] = {0.0}, tot[1];
-    for (int e = P.chunk_e0[chunk] + threadIdx.x; e < P.chunk_e1[chunk]; e += blockDim.x) comp_add(s[0], c[0], P.e_dh[e]);
-    (void)NP;
-    if (!chunk_finish<1>(P, chunk, inst, s, c, tot)) return;
+    if (P.mixed) {
+        // mixed form: Delta H carries FP32 rounding; double-float block sum on the FP32 pipe
+        df r = {0.0f, 0.0f};
+        float g = 0.0f, a = 0.0f;
+        for (int e = P.chunk_e0[chunk] + threadIdx.x; e < P.chunk_e1[chunk]; e += blockDim.x) r = df_add(r, df_from(P.e_dh[e]));
+        block_sum_df(r, g, a);
+        s[0] = (double)r.hi;
+        c[0] = (double)r.lo;
+        if (!chunk_publish<1>(P, chunk, inst, s, c, tot)) return;
+    } else {
+        for (int e = P.chunk_e0[chunk] + threadIdx.x; e < P.chunk_e1[chunk]; e += blockDim.x) comp_add(s[0], c[0], P.e_dh[e]);
+        if (!chunk_finish<1>(P, chunk, inst, s, c, tot)) return;
+    }
     InstScalars &S = P.scal[inst];
     S.dH = S.dt * tot[0];
     S.iters = 0;
@@ -324,27 +333,34 @@ __global__ void __launch_bounds__(256) k_update(const RelaxParams P) {
     const int chunk = blockIdx.x;
     const int inst = P.chunk_inst[chunk];
     const double gdt = P.scal[inst].gamma * P.scal[inst].dt;
-    const int needH = P.scal[inst].need_H;
+    const int needH = P.scal[inst].need_H;   // uniform per block
     const size_t NPtot = P.NE * NP;
     const size_t n0 = (size_t)P.chunk_e0[chunk] * NP, n1 = (size_t)P.chunk_e1[chunk] * NP;
     double s[2] = {0, 0}, c[2] = {0, 0}, tot[2];
     uint32_t bad = 0;
+    df R = {0.0f, 0.0f};
+    float A = 0.0f, G = 0.0f;
     for (size_t j = n0 + threadIdx.x; j < n1; j += blockDim.x) {
         double u[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             u[v] = fma(gdt, __ldg(P.d + v * NPtot + j), P.U[v * NPtot + j]);
             P.U[v * NPtot + j] = u[v];
-            if constexpr (DF) P.Uf[v * NPtot + j] = __double2float_rn(u[v]);
-            if (!isfinite(u[v])) bad |= PERRK_FLAG_NONFINITE;
+            if constexpr (DF) {
+                const float uf = __double2float_rn(u[v]);
+                P.Uf[v * NPtot + j] = uf;
+                if (!isfinite(uf)) bad |= PERRK_FLAG_NONFINITE;
+            } else {
+                if (!isfinite(u[v])) bad |= PERRK_FLAG_NONFINITE;
+            }
         }
         if (needH) {
             if constexpr (DF) {
                 float wd;
                 const df sv = df_entropy<DIM, EQ>(u, nullptr, P, wd, bad);
-                const double t = df_to(df_mul(sv, df_from(__ldg(P.wJ + j))));
-                comp_add(s[0], c[0], t);
-                comp_add(s[1], c[1], fabs(t));
+                const df t = df_mul(sv, df_from(__ldg(P.wJ + j)));
+                R = df_add(R, t);
+                A += fabsf(t.hi);
             } else {
                 double sv;
                 node_entropy<DIM, EQ>(u, P.gamma_gas, sv, nullptr, bad);
@@ -355,7 +371,29 @@ __global__ void __launch_bounds__(256) k_update(const RelaxParams P) {
         }
     }
     if (bad) atomicOr(P.flags, bad);
-    if (!chunk_finish<2>(P, chunk, inst, s, c, tot)) return;
+    if (needH) {
+        if constexpr (DF) {
+            block_sum_df(R, G, A);
+            s[0] = (double)R.hi;
+            c[0] = (double)R.lo;
+            s[1] = (double)A;
+            if (!chunk_publish<2>(P, chunk, inst, s, c, tot)) return;
+        } else {
+            if (!chunk_finish<2>(P, chunk, inst, s, c, tot)) return;
+        }
+    } else {
+        // no reduction: only the instance's last block does the bookkeeping
+        __shared__ int s_last;
+        if (threadIdx.x == 0) {
+            __threadfence();
+            const unsigned ticket = atomicAdd(P.counters + inst, 1u);
+            s_last = (ticket == (unsigned)P.inst_nchunks[inst] - 1u);
+        }
+        __syncthreads();
+        if (!s_last || threadIdx.x != 0) return;
+        __threadfence();
+        P.counters[inst] = 0u;
+    }
     InstScalars &S = P.scal[inst];
     double Hn1, An1;
     if (needH) {
@@ -406,6 +444,8 @@ __global__ void __launch_bounds__(256) k_entropy(const RelaxParams P) {
     const size_t n0 = (size_t)P.chunk_e0[chunk] * NP, n1 = (size_t)P.chunk_e1[chunk] * NP;
     double s[2] = {0, 0}, c[2] = {0, 0}, tot[2];
     uint32_t bad = 0;
+    df R = {0.0f, 0.0f};
+    float A = 0.0f, G = 0.0f;
     for (size_t j = n0 + threadIdx.x; j < n1; j += blockDim.x) {
         double u[V];
 #pragma unroll
@@ -413,9 +453,9 @@ __global__ void __launch_bounds__(256) k_entropy(const RelaxParams P) {
         if constexpr (DF) {
             float wd;
             const df sv = df_entropy<DIM, EQ>(u, nullptr, P, wd, bad);
-            const double t = df_to(df_mul(sv, df_from(__ldg(P.wJ + j))));
-            comp_add(s[0], c[0], t);
-            comp_add(s[1], c[1], fabs(t));
+            const df t = df_mul(sv, df_from(__ldg(P.wJ + j)));
+            R = df_add(R, t);
+            A += fabsf(t.hi);
         } else {
             double sv;
             node_entropy<DIM, EQ>(u, P.gamma_gas, sv, nullptr, bad);
@@ -425,7 +465,15 @@ __global__ void __launch_bounds__(256) k_entropy(const RelaxParams P) {
         }
     }
     if (bad) atomicOr(P.flags, bad);
-    if (!chunk_finish<2>(P, chunk, inst, s, c, tot)) return;
+    if constexpr (DF) {
+        block_sum_df(R, G, A);
+        s[0] = (double)R.hi;
+        c[0] = (double)R.lo;
+        s[1] = (double)A;
+        if (!chunk_publish<2>(P, chunk, inst, s, c, tot)) return;
+    } else {
+        if (!chunk_finish<2>(P, chunk, inst, s, c, tot)) return;
+    }
     InstScalars &S = P.scal[inst];
     if (P.query) {
         S.H_next = tot[0];
@@ -470,6 +518,7 @@ static RelaxParams relax_params(Ctx &c) {
     P.guess = c.opt.guess;
     P.target = c.opt.target;
     P.relax = c.opt.relaxation;
+    P.mixed = c.opt.precision == PERRK_MIXED ? 1 : 0;
     P.tol_r = c.opt.newton_tol_r;
     P.tol_g = c.opt.newton_tol_g;
     P.dftab = (const float4 *)c.g_dftab;

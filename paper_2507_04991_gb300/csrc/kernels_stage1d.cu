@@ -8,8 +8,20 @@ namespace perrk {
 
 template <int EQ, typename Real, bool CURVED>
 static cudaError_t go(const StageParams &P, int epb, int grid, cudaStream_t st) {
-    if (epb == 16) { k_stage<1, EQ, Real, CURVED, 16><<<grid, 16 * ipow4(1), 0, st>>>(P); return cudaGetLastError(); }
-    if (epb == 32) { k_stage<1, EQ, Real, CURVED, 32><<<grid, 32 * ipow4(1), 0, st>>>(P); return cudaGetLastError(); }
+    if (epb == 16) {
+        if constexpr (stage_smem_bytes<1, EQ, Real, CURVED, 16>() <= 48 * 1024) {
+            k_stage<1, EQ, Real, CURVED, 16><<<grid, 16 * ipow4(1), 0, st>>>(P);
+            return cudaGetLastError();
+        }
+        return cudaErrorInvalidConfiguration;
+    }
+    if (epb == 32) {
+        if constexpr (stage_smem_bytes<1, EQ, Real, CURVED, 32>() <= 48 * 1024) {
+            k_stage<1, EQ, Real, CURVED, 32><<<grid, 32 * ipow4(1), 0, st>>>(P);
+            return cudaGetLastError();
+        }
+        return cudaErrorInvalidConfiguration;
+    }
     return cudaErrorInvalidValue;
 }
 

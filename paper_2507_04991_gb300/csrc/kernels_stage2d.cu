@@ -8,9 +8,27 @@ namespace perrk {
 
 template <int EQ, typename Real, bool CURVED>
 static cudaError_t go(const StageParams &P, int epb, int grid, cudaStream_t st) {
-    if (epb == 4) { k_stage<2, EQ, Real, CURVED, 4><<<grid, 4 * ipow4(2), 0, st>>>(P); return cudaGetLastError(); }
-    if (epb == 8) { k_stage<2, EQ, Real, CURVED, 8><<<grid, 8 * ipow4(2), 0, st>>>(P); return cudaGetLastError(); }
-    if (epb == 16) { k_stage<2, EQ, Real, CURVED, 16><<<grid, 16 * ipow4(2), 0, st>>>(P); return cudaGetLastError(); }
+    if (epb == 4) {
+        if constexpr (stage_smem_bytes<2, EQ, Real, CURVED, 4>() <= 48 * 1024) {
+            k_stage<2, EQ, Real, CURVED, 4><<<grid, 4 * ipow4(2), 0, st>>>(P);
+            return cudaGetLastError();
+        }
+        return cudaErrorInvalidConfiguration;
+    }
+    if (epb == 8) {
+        if constexpr (stage_smem_bytes<2, EQ, Real, CURVED, 8>() <= 48 * 1024) {
+            k_stage<2, EQ, Real, CURVED, 8><<<grid, 8 * ipow4(2), 0, st>>>(P);
+            return cudaGetLastError();
+        }
+        return cudaErrorInvalidConfiguration;
+    }
+    if (epb == 16) {
+        if constexpr (stage_smem_bytes<2, EQ, Real, CURVED, 16>() <= 48 * 1024) {
+            k_stage<2, EQ, Real, CURVED, 16><<<grid, 16 * ipow4(2), 0, st>>>(P);
+            return cudaGetLastError();
+        }
+        return cudaErrorInvalidConfiguration;
+    }
     return cudaErrorInvalidValue;
 }
 

@@ -8,9 +8,27 @@ namespace perrk {
 
 template <int EQ, typename Real, bool CURVED>
 static cudaError_t go(const StageParams &P, int epb, int grid, cudaStream_t st) {
-    if (epb == 1) { k_stage<3, EQ, Real, CURVED, 1><<<grid, 1 * ipow4(3), 0, st>>>(P); return cudaGetLastError(); }
-    if (epb == 2) { k_stage<3, EQ, Real, CURVED, 2><<<grid, 2 * ipow4(3), 0, st>>>(P); return cudaGetLastError(); }
-    if (epb == 4) { k_stage<3, EQ, Real, CURVED, 4><<<grid, 4 * ipow4(3), 0, st>>>(P); return cudaGetLastError(); }
+    if (epb == 1) {
+        if constexpr (stage_smem_bytes<3, EQ, Real, CURVED, 1>() <= 48 * 1024) {
+            k_stage<3, EQ, Real, CURVED, 1><<<grid, 1 * ipow4(3), 0, st>>>(P);
+            return cudaGetLastError();
+        }
+        return cudaErrorInvalidConfiguration;
+    }
+    if (epb == 2) {
+        if constexpr (stage_smem_bytes<3, EQ, Real, CURVED, 2>() <= 48 * 1024) {
+            k_stage<3, EQ, Real, CURVED, 2><<<grid, 2 * ipow4(3), 0, st>>>(P);
+            return cudaGetLastError();
+        }
+        return cudaErrorInvalidConfiguration;
+    }
+    if (epb == 4) {
+        if constexpr (stage_smem_bytes<3, EQ, Real, CURVED, 4>() <= 48 * 1024) {
+            k_stage<3, EQ, Real, CURVED, 4><<<grid, 4 * ipow4(3), 0, st>>>(P);
+            return cudaGetLastError();
+        }
+        return cudaErrorInvalidConfiguration;
+    }
     return cudaErrorInvalidValue;
 }
 

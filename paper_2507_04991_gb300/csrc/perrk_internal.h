@@ -108,6 +108,7 @@ struct Ctx {
     float *Uf = nullptr, *K1f = nullptr, *Kaf = nullptr, *Kbf = nullptr;   // mixed form
     double *e_dh = nullptr;                   // [n_elem] per-element b-weighted <w, K> sums
     double *g_node = nullptr, *g_elem = nullptr, *g_fnorm = nullptr, *g_wJ = nullptr;
+    float *g_node_f = nullptr, *g_elem_f = nullptr, *g_fnorm_f = nullptr, *g_wJ_f = nullptr;
     int32_t *g_nbr = nullptr, *g_gp = nullptr, *g_elist = nullptr;
     int32_t *g_chunk_inst = nullptr, *g_chunk_e0 = nullptr, *g_chunk_e1 = nullptr;
     int32_t *g_inst_chunk0 = nullptr, *g_inst_nchunks = nullptr;

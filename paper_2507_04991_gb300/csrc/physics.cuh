@@ -20,12 +20,24 @@ template <> struct Lit<float> {
     static constexpr float series_u = 1e-2f;
 };
 
+// float64 path: IEEE operations.  FP32 path (mixed form): the single MUFU
+// approximations (reciprocal and square root within ~2 ulp, log2 within
+// ~2^-22 absolute); the logarithms only enter the logarithmic means away
+// from the series branch, where |log y - log x| >= 0.2.
 __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
-__device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ float rcp(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 __device__ __forceinline__ double dlog(double x) { return log(x); }
-__device__ __forceinline__ float dlog(float x) { return logf(x); }
+__device__ __forceinline__ float dlog(float x) { return __logf(x); }
 __device__ __forceinline__ double dsqrt(double x) { return sqrt(x); }
-__device__ __forceinline__ float dsqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ float dsqrt(float x) {
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 __device__ __forceinline__ double dfma(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float dfma(float a, float b, float c) { return fmaf(a, b, c); }
 

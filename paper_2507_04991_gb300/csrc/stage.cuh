@@ -35,10 +35,35 @@ struct StageParams {
     int stage1;                 // U_{n,1} = U_n: no K loads
     int do_b;                   // some element has b_i != 0 at this stage
     int es;                     // Rusanov dissipation on the surface flux
+    const float *g_node_f, *g_elem_f, *fnorm_f, *wJ_f;   // FP32 geometry (mixed form)
     double gamma_gas;
     double D[16];
     double w_end;
+    float Df[16];               // FP32 copies of the tables and constants (mixed form)
+    float inv_w_f, gm1_f, inv_gm1_f, gam_f;
     uint32_t *flags;
+};
+
+// Geometry and constants in the kernel's arithmetic type, without per-use
+// float64 -> float conversions in the mixed form.
+template <typename Real>
+struct Geo {
+    __device__ static Real node(const StageParams &P, int c, size_t NPtot, size_t idx) {
+        if constexpr (sizeof(Real) == 8) return __ldg(P.g_node + c * NPtot + idx);
+        else return __ldg(P.g_node_f + c * NPtot + idx);
+    }
+    __device__ static Real elem(const StageParams &P, size_t e, int c) {
+        if constexpr (sizeof(Real) == 8) return __ldg(P.g_elem + e * 8 + c);
+        else return __ldg(P.g_elem_f + e * 8 + c);
+    }
+    __device__ static Real fn(const StageParams &P, size_t i) {
+        if constexpr (sizeof(Real) == 8) return __ldg(P.fnorm + i);
+        else return __ldg(P.fnorm_f + i);
+    }
+    __device__ static Real D(const StageParams &P, int i) {
+        if constexpr (sizeof(Real) == 8) return P.D[i];
+        else return P.Df[i];
+    }
 };
 
 template <int DIM>
@@ -100,6 +125,17 @@ __device__ __forceinline__ void stage_state(const StageParams &P, size_t NPtot, 
     }
 }
 
+// Static shared memory of k_stage (must stay within the 48 KiB static limit).
+template <int DIM, int EQ, typename Real, bool CURVED, int EPB>
+constexpr size_t stage_smem_bytes() {
+    constexpr int NP = ipow4(DIM), NF = 2 * DIM, NFP = ipow4(DIM - 1);
+    constexpr int V = EQ == EQ_BURGERS ? 1 : DIM + 2;
+    constexpr int NPR = EQ == EQ_BURGERS ? 1 : DIM + 5;
+    constexpr int NPAIR = DIM * ipow4(DIM - 1) * 6;
+    return sizeof(Real) * (size_t)EPB * (V * NP + NPR * NP + NF * NFP * V + (CURVED ? 4 : 1) * NP + NPAIR * V) +
+           sizeof(double) * (size_t)EPB * NP;
+}
+
 template <int DIM, int EQ, typename Real, bool CURVED, int EPB>
 __global__ void __launch_bounds__(EPB * ipow4(DIM)) k_stage(const StageParams P) {
     constexpr int NP = ipow4(DIM), NF = 2 * DIM, NFP = ipow4(DIM - 1);
@@ -110,11 +146,24 @@ __global__ void __launch_bounds__(EPB * ipow4(DIM)) k_stage(const StageParams P)
     __shared__ Real s_sf[EPB][NF * NFP][V];
     __shared__ Real s_ja[EPB][CURVED ? 4 : 1][NP];
     __shared__ double s_red[EPB][NP];
+    constexpr int NLINE = DIM * ipow4(DIM - 1);       // reference lines per element
+    constexpr int NPAIR = NLINE * 6;                  // node pairs (q < m) on those lines
+    __shared__ Real s_pf[EPB][NPAIR][V];              // two-point volume fluxes, one per pair
 
     const int el = threadIdx.x / NP, q = threadIdx.x % NP;
     const size_t NPtot = P.NE * NP;
-    const Real gm1 = Real(P.gamma_gas - 1.0), inv_gm1 = Real(1.0 / (P.gamma_gas - 1.0)), gam = Real(P.gamma_gas);
-    const Real inv_w = Real(1.0 / P.w_end);
+    Real gm1, inv_gm1, gam, inv_w;
+    if constexpr (sizeof(Real) == 8) {
+        gm1 = P.gamma_gas - 1.0;
+        inv_gm1 = 1.0 / (P.gamma_gas - 1.0);
+        gam = P.gamma_gas;
+        inv_w = 1.0 / P.w_end;
+    } else {
+        gm1 = P.gm1_f;
+        inv_gm1 = P.inv_gm1_f;
+        gam = P.gam_f;
+        inv_w = P.inv_w_f;
+    }
     uint32_t bad = 0;
     const int ngroups = (P.n_active + EPB - 1) / EPB;
 
@@ -125,7 +174,21 @@ __global__ void __launch_bounds__(EPB * ipow4(DIM)) k_stage(const StageParams P)
         const int g = P.gp[e];
         const size_t idx = (size_t)e * NP + q;
 
-        // ---- A: own stage state
+        // ---- A: own stage state; the neighbour face states this thread needs
+        // in phase B are loaded first so that their latency overlaps phase A
+        constexpr int NSLOT = (NF * NFP + NP - 1) / NP;
+        Real un_pre[NSLOT][V];
+#pragma unroll
+        for (int t = 0; t < NSLOT; ++t) {
+            const int sl = q + t * NP;
+            if (sl < NF * NFP) {
+                const int f = sl / NFP, kk = sl % NFP;
+                const int nb = P.nbr[(size_t)e * NF + f];
+                const int qn = face_node_dev<DIM>(f ^ 1, kk);
+                double t0[V], t1[V], t2[V];
+                stage_state<V, Real>(P, NPtot, (size_t)nb * NP + qn, P.gp[nb], un_pre[t], t0, t1, t2);
+            }
+        }
         Real u[V];
         double Ud[V], K1d[V], Kpd[V];
         stage_state<V, Real>(P, NPtot, idx, g, u, Ud, K1d, Kpd);
@@ -144,33 +207,32 @@ __global__ void __launch_bounds__(EPB * ipow4(DIM)) k_stage(const StageParams P)
         Real invJ, Jak_box[DIM > 0 ? DIM : 1];
         if constexpr (CURVED) {
 #pragma unroll
-            for (int c = 0; c < 4; ++c) s_ja[el][c][q] = (Real)__ldg(P.g_node + c * NPtot + idx);
-            invJ = (Real)__ldg(P.g_node + 4 * NPtot + idx);
+            for (int c = 0; c < 4; ++c) s_ja[el][c][q] = Geo<Real>::node(P, c, NPtot, idx);
+            invJ = Geo<Real>::node(P, 4, NPtot, idx);
         } else {
 #pragma unroll
-            for (int a = 0; a < DIM; ++a) Jak_box[a] = (Real)__ldg(P.g_elem + (size_t)e * 8 + a);
-            invJ = (Real)__ldg(P.g_elem + (size_t)e * 8 + 3);
+            for (int a = 0; a < DIM; ++a) Jak_box[a] = Geo<Real>::elem(P, (size_t)e, a);
+            invJ = Geo<Real>::elem(P, (size_t)e, 3);
         }
         __syncthreads();
 
         // ---- B: interface fluxes at this element's face nodes
-        for (int sl = q; sl < NF * NFP; sl += NP) {
+#pragma unroll
+        for (int t = 0; t < NSLOT; ++t) {
+            const int sl = q + t * NP;
+            if (sl >= NF * NFP) break;
             const int f = sl / NFP, kk = sl % NFP;
             const int qs = face_node_dev<DIM>(f, kk);
-            const int nb = P.nbr[(size_t)e * NF + f];
-            const int qn = face_node_dev<DIM>(f ^ 1, kk);
-            Real un[V];
-            double t0[V], t1[V], t2[V];
-            stage_state<V, Real>(P, NPtot, (size_t)nb * NP + qn, P.gp[nb], un, t0, t1, t2);
+            const Real *un = un_pre[t];
             Real us[V];
 #pragma unroll
             for (int v = 0; v < V; ++v) us[v] = s_u[el][v][qs];
             Real nrm[DIM];
             if constexpr (CURVED) {
-                nrm[0] = (Real)__ldg(P.fnorm + (((size_t)e * NF + f) * NFP + kk) * 2 + 0);
-                nrm[1 % DIM] = (Real)__ldg(P.fnorm + (((size_t)e * NF + f) * NFP + kk) * 2 + 1);
+                nrm[0] = Geo<Real>::fn(P, (((size_t)e * NF + f) * NFP + kk) * 2 + 0);
+                nrm[1 % DIM] = Geo<Real>::fn(P, (((size_t)e * NF + f) * NFP + kk) * 2 + 1);
             } else {
-                nrm[0] = (Real)__ldg(P.fnorm + (size_t)e * NF + f);
+                nrm[0] = Geo<Real>::fn(P, (size_t)e * NF + f);
             }
             const bool self_plus = (f & 1);
             const Real *uL = self_plus ? us : un;
@@ -227,7 +289,64 @@ __global__ void __launch_bounds__(EPB * ipow4(DIM)) k_stage(const StageParams P)
             for (int v = 0; v < V; ++v) s_sf[el][sl][v] = sg * (fs[v] - fp[v]) * inv_w;
         }
 
-        // ---- C: volume flux differencing along each reference direction
+        // ---- C: volume flux differencing.  The two-point flux is symmetric,
+        // so each pair (q, m) on a reference line is evaluated once (pairs
+        // spread over the element's threads) and used by both nodes.
+        for (int pp = q; pp < NPAIR; pp += NP) {
+            const int k = pp / (NPAIR / DIM), line = (pp % (NPAIR / DIM)) / 6, lp = pp % 6;
+            const int a = lp < 3 ? 0 : (lp < 5 ? 1 : 2);
+            const int b = lp < 3 ? lp + 1 : (lp < 5 ? lp - 1 : 3);
+            // nodes with index a / b along direction k on this line
+            int qa, qb;
+            if (DIM == 1) {
+                qa = a;
+                qb = b;
+            } else if (DIM == 2) {
+                qa = k == 0 ? a + 4 * line : line + 4 * a;
+                qb = k == 0 ? b + 4 * line : line + 4 * b;
+            } else {
+                const int l0 = line & 3, l1 = line >> 2;
+                qa = k == 0 ? a + 4 * l0 + 16 * l1 : (k == 1 ? l0 + 4 * a + 16 * l1 : l0 + 4 * l1 + 16 * a);
+                qb = k == 0 ? b + 4 * l0 + 16 * l1 : (k == 1 ? l0 + 4 * b + 16 * l1 : l0 + 4 * l1 + 16 * b);
+            }
+            Real F[V];
+            if constexpr (EQ == EQ_BURGERS) {
+                const Real ua = s_u[el][0][qa], ub = s_u[el][0][qb];
+                F[0] = (ua * ua + ua * ub + ub * ub) * Real(1.0 / 6.0) * Jak_box[0];
+            } else {
+                constexpr int DD = EQ == EQ_EULER ? DIM : 1;
+                Prim<Real, DD> pa, pb;
+                pa.rho = s_pr[el][0][qa];
+                pb.rho = s_pr[el][0][qb];
+#pragma unroll
+                for (int c = 0; c < DD; ++c) {
+                    pa.v[c] = s_pr[el][1 + c][qa];
+                    pb.v[c] = s_pr[el][1 + c][qb];
+                }
+                pa.p = s_pr[el][DD + 1][qa];
+                pb.p = s_pr[el][DD + 1][qb];
+                pa.beta = s_pr[el][DD + 2][qa];
+                pb.beta = s_pr[el][DD + 2][qb];
+                pa.lrho = s_pr[el][DD + 3][qa];
+                pb.lrho = s_pr[el][DD + 3][qb];
+                pa.lbeta = s_pr[el][DD + 4][qa];
+                pb.lbeta = s_pr[el][DD + 4][qb];
+                Real nv[DD];
+                if constexpr (CURVED) {
+                    nv[0] = Real(0.5) * (s_ja[el][2 * k][qa] + s_ja[el][2 * k][qb]);
+                    nv[1 % DD] = Real(0.5) * (s_ja[el][2 * k + 1][qa] + s_ja[el][2 * k + 1][qb]);
+                    ranocha<Real, DD, -1>(pa, pb, nv, inv_gm1, F);
+                } else {
+                    nv[0] = Jak_box[k];
+                    if (k == 0) ranocha<Real, DD, 0>(pa, pb, nv, inv_gm1, F);
+                    else if (k == 1) ranocha<Real, DD, (1 < DD ? 1 : 0)>(pa, pb, nv, inv_gm1, F);
+                    else ranocha<Real, DD, (2 < DD ? 2 : 0)>(pa, pb, nv, inv_gm1, F);
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < V; ++v) s_pf[el][pp][v] = F[v];
+        }
+        __syncthreads();
         Real acc[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) acc[v] = 0;
@@ -235,57 +354,41 @@ __global__ void __launch_bounds__(EPB * ipow4(DIM)) k_stage(const StageParams P)
 #pragma unroll
         for (int k = 0; k < DIM; ++k) {
             const int ik = id[k];
-            const int stride = 1 << (2 * k);
+            const int line = DIM == 1 ? 0 : (DIM == 2 ? (k == 0 ? id[1] : id[0])
+                                                      : (k == 0 ? id[1] + 4 * id[2] : (k == 1 ? id[0] + 4 * id[2] : id[0] + 4 * id[1])));
+            const int base = k * (NPAIR / DIM) + line * 6;
 #pragma unroll
             for (int m = 0; m < 4; ++m) {
-                const int qm = q + (m - ik) * stride;
-                const Real Dv = Real(2.0) * (Real)P.D[ik * 4 + m];
+                if (m == ik) continue;
+                const int lo = m < ik ? m : ik, hi = m < ik ? ik : m;
+                const int lp = lo == 0 ? hi - 1 : (lo == 1 ? hi + 1 : 5);
+                const Real Dv = Real(2.0) * Geo<Real>::D(P, ik * 4 + m);
+#pragma unroll
+                for (int v = 0; v < V; ++v) acc[v] = dfma(Dv, s_pf[el][base + lp][v], acc[v]);
+            }
+            if (ik == 0 || ik == 3) {
+                // diagonal term 2 D_qq f(U_q) . Ja^k_q (consistency of the two-point flux)
+                const Real Dv = Real(2.0) * Geo<Real>::D(P, ik * 4 + ik);
                 Real F[V];
                 if constexpr (EQ == EQ_BURGERS) {
-                    const Real a = u[0], b = s_u[el][0][qm];
-                    if (m == ik) {
-                        if (ik != 0 && ik != 3) continue;
-                        F[0] = Real(0.5) * a * a;
-                    } else {
-                        F[0] = (a * a + a * b + b * b) * Real(1.0 / 6.0);
-                    }
-                    F[0] *= (CURVED ? Real(1) : Jak_box[0]);
+                    F[0] = Real(0.5) * u[0] * u[0] * Jak_box[0];
                 } else {
                     constexpr int DD = EQ == EQ_EULER ? DIM : 1;
-                    Prim<Real, DD> pq, pm;
+                    Prim<Real, DD> pq;
                     pq.rho = s_pr[el][0][q];
-                    pm.rho = s_pr[el][0][qm];
 #pragma unroll
-                    for (int a = 0; a < DD; ++a) {
-                        pq.v[a] = s_pr[el][1 + a][q];
-                        pm.v[a] = s_pr[el][1 + a][qm];
-                    }
+                    for (int c = 0; c < DD; ++c) pq.v[c] = s_pr[el][1 + c][q];
                     pq.p = s_pr[el][DD + 1][q];
-                    pm.p = s_pr[el][DD + 1][qm];
-                    pq.beta = s_pr[el][DD + 2][q];
-                    pm.beta = s_pr[el][DD + 2][qm];
-                    pq.lrho = s_pr[el][DD + 3][q];
-                    pm.lrho = s_pr[el][DD + 3][qm];
-                    pq.lbeta = s_pr[el][DD + 4][q];
-                    pm.lbeta = s_pr[el][DD + 4][qm];
                     Real nv[DD];
                     if constexpr (CURVED) {
-                        nv[0] = Real(0.5) * (s_ja[el][2 * k][q] + s_ja[el][2 * k][qm]);
-                        nv[1 % DD] = Real(0.5) * (s_ja[el][2 * k + 1][q] + s_ja[el][2 * k + 1][qm]);
+                        nv[0] = s_ja[el][2 * k][q];
+                        nv[1 % DD] = s_ja[el][2 * k + 1][q];
+                        euler_flux<Real, DD, -1>(u, pq, nv, F);
                     } else {
                         nv[0] = Jak_box[k];
-                    }
-                    if (m == ik) {
-                        if (ik != 0 && ik != 3) continue;
-                        if constexpr (CURVED) euler_flux<Real, DD, -1>(u, pq, nv, F);
-                        else if (k == 0) euler_flux<Real, DD, 0>(u, pq, nv, F);
+                        if (k == 0) euler_flux<Real, DD, 0>(u, pq, nv, F);
                         else if (k == 1) euler_flux<Real, DD, (1 < DD ? 1 : 0)>(u, pq, nv, F);
                         else euler_flux<Real, DD, (2 < DD ? 2 : 0)>(u, pq, nv, F);
-                    } else {
-                        if constexpr (CURVED) ranocha<Real, DD, -1>(pq, pm, nv, inv_gm1, F);
-                        else if (k == 0) ranocha<Real, DD, 0>(pq, pm, nv, inv_gm1, F);
-                        else if (k == 1) ranocha<Real, DD, (1 < DD ? 1 : 0)>(pq, pm, nv, inv_gm1, F);
-                        else ranocha<Real, DD, (2 < DD ? 2 : 0)>(pq, pm, nv, inv_gm1, F);
                     }
                 }
 #pragma unroll
@@ -360,9 +463,9 @@ __global__ void __launch_bounds__(EPB * ipow4(DIM)) k_stage(const StageParams P)
                         // w_m . K_m + w_E K_E = (gamma-1) rho / p (v . K_m - K_E)
                         wdf = dfma(w0, k0, gm1 * rho * ip * (mk - kE));
                     }
-                    wdot = (double)wdf;
+                    wdot = (double)(wdf * __ldg(P.wJ_f + idx));
                 }
-                wdot *= __ldg(P.wJ + idx);
+                if constexpr (sizeof(Real) == 8) wdot *= __ldg(P.wJ + idx);
                 if (valid) {
 #pragma unroll
                     for (int v = 0; v < V; ++v) {

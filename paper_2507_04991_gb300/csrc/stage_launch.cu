@@ -61,15 +61,27 @@ perrk_status launch_stage(Ctx &c, int stage, bool rhs_only, const double *in_u, 
     P.do_b = (!rhs_only && c.any_b[stage]) ? 1 : 0;
     P.es = c.surface == PERRK_SURFACE_ES_RUSANOV ? 1 : 0;
     P.gamma_gas = c.gamma_gas;
-    for (int i = 0; i < 16; ++i) P.D[i] = c.lgl_D[i];
+    for (int i = 0; i < 16; ++i) {
+        P.D[i] = c.lgl_D[i];
+        P.Df[i] = (float)c.lgl_D[i];
+    }
     P.w_end = c.lgl_w[0];
+    P.inv_w_f = (float)(1.0 / c.lgl_w[0]);
+    P.gm1_f = (float)(c.gamma_gas - 1.0);
+    P.inv_gm1_f = (float)(1.0 / (c.gamma_gas - 1.0));
+    P.gam_f = (float)c.gamma_gas;
+    P.g_node_f = c.g_node_f;
+    P.g_elem_f = c.g_elem_f;
+    P.fnorm_f = c.g_fnorm_f;
+    P.wJ_f = c.g_wJ_f;
     P.flags = c.g_flags;
     if (P.n_active <= 0) return PERRK_OK;
     if (c.curved && c.dim != 2) {
         set_error("curved geometry is only implemented in 2D");
         return PERRK_NOT_SUPPORTED;
     }
-    if ((c.curved && (!c.g_node || !c.g_fnorm)) || (!c.curved && (!c.g_elem || !c.g_fnorm))) {
+    if ((c.curved && (!c.g_node || !c.g_fnorm)) || (!c.curved && (!c.g_elem || !c.g_fnorm)) ||
+        (mixed && (!c.g_wJ_f || !c.g_fnorm_f || (c.curved ? !c.g_node_f : !c.g_elem_f)))) {
         set_error("geometry tables missing for the selected geometry mode");
         return PERRK_INVALID_ARG;
     }

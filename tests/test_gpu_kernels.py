@@ -43,3 +43,22 @@ def test_repeatable_bitwise():
         outs.append((s.state(), [r[0]["gamma"] for r in recs]))
         s.close()
     assert np.array_equal(outs[0][0], outs[1][0]) and outs[0][1] == outs[1][1]
+
+
+@pytest.mark.parametrize("precision", [pk.FP64, pk.MIXED])
+def test_autotune_keeps_results_bitwise(precision):
+    wl = workloads.small_box_2d(n=8, seed=43, R=2, E=[6, 3], order=3)
+    s1 = pk.Solver(wl, pk.options(precision=precision))
+    r1 = s1.step(4)
+    u1 = s1.state()
+    s1.close()
+    s2 = pk.Solver(wl, pk.options(precision=precision, use_graph=True))
+    pk.perrk_autotune(s2.h)
+    s2.set_state(wl.u0)
+    tuning = pk.perrk_tuning(s2.h)
+    r2 = s2.step(4)
+    u2 = s2.state()
+    s2.close()
+    assert tuning["elems_per_cta"] in (4, 8, 16) and tuning["relax_threads"] in (128, 256)
+    assert np.array_equal(u1, u2)
+    assert [a[0]["gamma"] for a in r1] == [a[0]["gamma"] for a in r2]
