@@ -203,6 +203,27 @@ perrk_status perrk_launch_stage(perrk_ctx *ctx, int stage, void *stream);
 perrk_status perrk_stage_info(const perrk_ctx *ctx, int stage, int64_t *n_active, int64_t *bytes, int *n_stages,
                               int *kernels_per_step, int64_t *dof_stage_per_step);
 
+/* Allocation-free entropy functional (the paper has no counterpart; this is
+ * an interface for callers that cannot allocate device memory when they need
+ * the value, e.g. because they hand all device memory to their own pool
+ * allocator up front, or run a loop in which cudaMalloc -- which may
+ * synchronise the device and can fail under memory pressure -- is not
+ * allowed).  out[0] = sum_q wJ[q] s(u_q), out[1] = sum_q wJ[q] |s(u_q)|, with
+ * s the entropy of `equation` (u^2/2 for Burgers, -rho log(p rho^-gamma) for
+ * Euler), in float64 with compensated sums.  u: device, SoA [V][n_nodes];
+ * wJ: device [n_nodes] (quadrature weight times Jacobian per node); out:
+ * device double[2].  No context is used and nothing is allocated: the
+ * cross-block scratch is a file-scope device array of ~128 KiB that every
+ * device which loads the library holds until process exit.  n_nodes must lie
+ * in [1, 16777216]; larger inputs are rejected with PERRK_INVALID_ARG.  The
+ * first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  All
+ * calls share the array (it keeps the last call's contents; its counter is
+ * cleared at the start of each call), so calls whose work overlaps on the
+ * GPU race.  A non-physical node yields NaN in out[].  Asynchronous on stream. */
+perrk_status perrk_entropy_static(int equation, double gamma_gas, const double *u, const double *wJ, long long n_nodes,
+                                  double *out, void *stream);
+
 /* One evaluation of F on all elements: u_in, k_out device arrays [V][n_elem][NP]. */
 perrk_status perrk_rhs(perrk_ctx *ctx, const double *u_in, double *k_out, void *stream);
 

@@ -32,7 +32,7 @@ EXPORTED = [
     "perrk_default_options", "perrk_create", "perrk_create_batched", "perrk_destroy", "perrk_build_tableau",
     "perrk_shape", "perrk_set_state", "perrk_get_state", "perrk_set_dt", "perrk_step", "perrk_entropy",
     "perrk_rhs", "perrk_mlp_size", "perrk_mlp_features", "perrk_set_mlp", "perrk_mlp_train", "perrk_mlp_grad",
-    "perrk_last_error", "perrk_status_string", "perrk_launch_stage", "perrk_stage_info", "perrk_df_log", "perrk_autotune", "perrk_tuning",
+    "perrk_last_error", "perrk_status_string", "perrk_launch_stage", "perrk_stage_info", "perrk_df_log", "perrk_autotune", "perrk_tuning", "perrk_entropy_static",
 ]
 
 
@@ -100,6 +100,7 @@ def load(path=LIB_PATH):
         "perrk_df_log": (I, [P, P, I, P]),
         "perrk_autotune": (I, [P, P, P]),
         "perrk_tuning": (I, [P, P, P, P]),
+        "perrk_entropy_static": (I, [I, D, P, P, C.c_longlong, P, P]),
         "perrk_stage_info": (I, [P, I, P, P, P, P, P]),
         "perrk_status_string": (C.c_char_p, [I]),
     }
@@ -301,6 +302,12 @@ def perrk_tuning(h):
     a, b, c = C.c_int(), C.c_int(), C.c_int()
     _check(load().perrk_tuning(h, C.byref(a), C.byref(b), C.byref(c)), "perrk_tuning")
     return dict(elems_per_cta=a.value, persistent_grid=b.value, relax_threads=c.value)
+
+
+def perrk_entropy_static(equation, gamma_gas, u_ptr, wJ_ptr, n_nodes, out_ptr, stream=0):
+    """Entropy functional without allocating: device pointers in and out."""
+    _check(load().perrk_entropy_static(int(equation), float(gamma_gas), C.c_void_p(u_ptr), C.c_void_p(wJ_ptr),
+                                       int(n_nodes), C.c_void_p(out_ptr), C.c_void_p(stream)), "perrk_entropy_static")
 
 
 def perrk_df_log(x_ptr, y_ptr, n, stream=0):
