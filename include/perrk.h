@@ -114,8 +114,10 @@ typedef struct {
     double H_next;                /* H(U_{n+1}) */
     double t;                     /* time after the step, t_n + gamma dt */
     double gamma_guess;           /* initial Newton guess used */
+    double gamma_prev;            /* gamma_{n-1}: the last converged gamma before this step (1 at the start) */
     int32_t newton_iters;         /* full-state Newton passes */
     uint32_t flags;               /* PERRK_FLAG_* */
+    float features[6];            /* learned-guess features of this step (see perrk_mlp_features) */
 } perrk_step_info;
 
 typedef struct perrk_ctx perrk_ctx;
@@ -227,8 +229,13 @@ perrk_status perrk_entropy_static(int equation, double gamma_gas, const double *
 /* One evaluation of F on all elements: u_in, k_out device arrays [V][n_elem][NP]. */
 perrk_status perrk_rhs(perrk_ctx *ctx, const double *u_in, double *k_out, void *stream);
 
-/* Learned Newton guess (spec form 4): a 2x64 tanh MLP on the features of
- * perrk_mlp_features.  weights: host float32 array of perrk_mlp_size() values
+/* Learned Newton guess (spec form 4): a 2x64 tanh MLP on F = 6 features
+ * available before the first Newton pass of step n, all from quantities the
+ * step has already computed: (gamma_{n-1} - 1, gamma_{n-2} - 1, gamma_{n-3} - 1,
+ * Delta H_n / A_n, (Delta H / A)_{n-1}, (Delta H / A)_{n-2}) with
+ * A = sum omega J |s(U)|; it predicts gamma_n - gamma_{n-1} and the guess is
+ * gamma_{n-1} + prediction.  The Newton iteration then runs unchanged, so the
+ * converged gamma does not depend on the guess.  weights: host float32 array of perrk_mlp_size() values
  * laid out W1[64][F], b1[64], W2[64][64], b2[64], W3[64], b3, then F input
  * means, F input scales, an output scale; NULL disables it. */
 int perrk_mlp_size(void);

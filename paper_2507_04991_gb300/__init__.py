@@ -55,8 +55,8 @@ class perrk_options(C.Structure):
 
 class perrk_step_info(C.Structure):
     _fields_ = [("gamma", C.c_double), ("H_n", C.c_double), ("dH", C.c_double), ("H_next", C.c_double),
-                ("t", C.c_double), ("gamma_guess", C.c_double), ("newton_iters", C.c_int32),
-                ("flags", C.c_uint32)]
+                ("t", C.c_double), ("gamma_guess", C.c_double), ("gamma_prev", C.c_double),
+                ("newton_iters", C.c_int32), ("flags", C.c_uint32), ("features", C.c_float * 6)]
 
 
 class PerrkError(RuntimeError):
@@ -264,7 +264,8 @@ def perrk_step(h, nsteps, info=True, stream=0):
         for i in range(n_inst):
             r = recs[k * n_inst + i]
             row.append(dict(gamma=r.gamma, H_n=r.H_n, dH=r.dH, H_next=r.H_next, t=r.t, gamma_guess=r.gamma_guess,
-                            iters=r.newton_iters, flags=r.flags))
+                            gamma_prev=r.gamma_prev, iters=r.newton_iters, flags=r.flags,
+                            features=[float(x) for x in r.features]))
         out.append(row)
     return out
 
@@ -349,6 +350,56 @@ def perrk_mlp_grad(feats, target, weights, stream=0):
     _check(load().perrk_mlp_grad(_ptr(X), _ptr(T), len(T), _ptr(W), _ptr(G), C.byref(loss), C.c_void_p(stream)),
            "perrk_mlp_grad")
     return G, loss.value
+
+
+# ------------------------------------------------------------ learned guess
+
+MLP_F, MLP_H = 6, 64
+
+
+def mlp_init(seed=0):
+    """Random initial weights (Glorot-uniform) in the library's layout, with
+    identity normalisation (mean 0, scale 1, output scale 1)."""
+    rng = np.random.default_rng(seed)
+    F, H = MLP_F, MLP_H
+    W1 = rng.uniform(-1, 1, (H, F)) * np.sqrt(6.0 / (F + H))
+    W2 = rng.uniform(-1, 1, (H, H)) * np.sqrt(6.0 / (2 * H))
+    W3 = rng.uniform(-1, 1, H) * np.sqrt(6.0 / (H + 1))
+    return np.concatenate([W1.ravel(), np.zeros(H), W2.ravel(), np.zeros(H), W3, [0.0],
+                           np.zeros(F), np.ones(F), [1.0]]).astype(np.float32)
+
+
+def mlp_dataset(records):
+    """(features, target) pairs from step records of converged steps: the
+    target is gamma_n - gamma_{n-1}."""
+    X, T = [], []
+    for row in records:
+        for r in row:
+            if r["flags"] & FLAG_NEWTON_FALLBACK:
+                continue
+            X.append(r["features"])
+            T.append(r["gamma"] - r["gamma_prev"])
+    return np.asarray(X, dtype=np.float64), np.asarray(T, dtype=np.float64)
+
+
+def mlp_fit(X, T, epochs=400, lr=3e-3, seed=0, stream=0):
+    """Normalise the data, train on the device (perrk_mlp_train) and return
+    weights ready for perrk_set_mlp (normalisation folded into the layout)."""
+    mean = X.mean(axis=0)
+    scale = X.std(axis=0)
+    scale[scale == 0] = 1.0
+    out_scale = float(np.abs(T).max()) or 1.0
+    W = mlp_init(seed)
+    F, H = MLP_F, MLP_H
+    Xn = ((X - mean) / scale).astype(np.float32)
+    Tn = (T / out_scale).astype(np.float32)
+    W, loss = perrk_mlp_train(Xn, Tn, W, epochs, lr, stream)
+    W = W.copy()
+    off = H * F + H + H * H + H + H + 1
+    W[off:off + F] = mean
+    W[off + F:off + 2 * F] = scale
+    W[off + 2 * F] = out_scale
+    return W, loss
 
 
 # ------------------------------------------------------------ convenience

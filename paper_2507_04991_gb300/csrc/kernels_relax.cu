@@ -211,6 +211,12 @@ __global__ void k_relax_init(const RelaxParams P) {
     }
     InstScalars &S = P.scal[inst];
     S.dH = S.dt * tot[0];
+    S.feat[0] = S.hist_gamma[0] - 1.0;
+    S.feat[1] = S.hist_gamma[1] - 1.0;
+    S.feat[2] = S.hist_gamma[2] - 1.0;
+    S.feat[3] = S.A_n > 0.0 ? S.dH / S.A_n : 0.0;
+    S.feat[4] = S.hist_dh[0];
+    S.feat[5] = S.hist_dh[1];
     S.iters = 0;
     S.flags = 0;
     S.converged = 0;
@@ -416,8 +422,10 @@ __global__ void __launch_bounds__(256) k_update(const RelaxParams P) {
         R.H_next = Hn1;
         R.t = S.t;
         R.gamma_guess = S.gamma_guess;
+        R.gamma_prev = S.hist_gamma[0];
         R.newton_iters = S.iters;
         R.flags = fl;
+        for (int k = 0; k < 6; ++k) R.features[k] = (float)S.feat[k];
     }
     if (P.relax) {
         if (S.converged) {

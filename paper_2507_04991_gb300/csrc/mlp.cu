@@ -29,9 +29,7 @@ __global__ void k_mlp_guess(const float *__restrict__ W, InstScalars *scal, int 
     if (inst >= n_inst) return;
     InstScalars &S = scal[inst];
     if (j == 0) {
-        const double raw[F] = {S.hist_gamma[0] - 1.0, S.hist_gamma[1] - 1.0, S.hist_gamma[2] - 1.0,
-                               S.A_n > 0.0 ? S.dH / S.A_n : 0.0, S.hist_dh[0], S.hist_dh[1]};
-        for (int f = 0; f < F; ++f) x[f] = (float)((raw[f] - (double)W[oMean + f]) / (double)W[oScale + f]);
+        for (int f = 0; f < F; ++f) x[f] = (float)((S.feat[f] - (double)W[oMean + f]) / (double)W[oScale + f]);
     }
     __syncthreads();
     float z = W[ob1 + j];

@@ -54,6 +54,7 @@ struct InstScalars {
     double hist_gamma[3];  // gamma_{n-1}, gamma_{n-2}, gamma_{n-3}
     double hist_dh[3];     // (Delta H / A)_{n}, _{n-1}, _{n-2} after the step
     double H_next;
+    double feat[6];        // learned-guess features of the current step
     int32_t iters;
     int32_t done;
     int32_t converged;
