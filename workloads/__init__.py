@@ -85,17 +85,16 @@ def structured_faces(n):
     """Periodic face list for an n[0] x n[1] x n[2] element grid (missing dims = 1)."""
     dim = len(n)
     nn = list(n) + [1] * (3 - dim)
-    rows = []
-    for iz in range(nn[2]):
-        for iy in range(nn[1]):
-            for ix in range(nn[0]):
-                e = _elem_index(ix, iy, iz, nn)
-                rows.append((e, 1, _elem_index((ix + 1) % nn[0], iy, iz, nn), 0))
-                if dim >= 2:
-                    rows.append((e, 3, _elem_index(ix, (iy + 1) % nn[1], iz, nn), 2))
-                if dim >= 3:
-                    rows.append((e, 5, _elem_index(ix, iy, (iz + 1) % nn[2], nn), 4))
-    return np.asarray(rows, dtype=np.int32)
+    iz, iy, ix = np.meshgrid(np.arange(nn[2]), np.arange(nn[1]), np.arange(nn[0]), indexing="ij")
+    ix, iy, iz = ix.ravel(), iy.ravel(), iz.ravel()
+    e = _elem_index(ix, iy, iz, nn)
+    cols = [np.stack([e, np.full_like(e, 1), _elem_index((ix + 1) % nn[0], iy, iz, nn), np.zeros_like(e)], 1)]
+    if dim >= 2:
+        cols.append(np.stack([e, np.full_like(e, 3), _elem_index(ix, (iy + 1) % nn[1], iz, nn), np.full_like(e, 2)], 1))
+    if dim >= 3:
+        cols.append(np.stack([e, np.full_like(e, 5), _elem_index(ix, iy, (iz + 1) % nn[2], nn), np.full_like(e, 4)], 1))
+    # rows ordered element by element, directions in turn
+    return np.stack(cols, 1).reshape(-1, 4).astype(np.int32)
 
 
 def tensor_coords(edges):
@@ -103,24 +102,20 @@ def tensor_coords(edges):
     dim = len(edges)
     n = [len(e) - 1 for e in edges]
     nn = n + [1] * (3 - dim)
-    NP = 4 ** dim
-    out = np.empty((int(np.prod(n)), NP, dim))
     t = 0.5 * (REF_NODES + 1.0)
     per_axis = []
     for a in range(dim):
         lo = np.asarray(edges[a][:-1])
         hi = np.asarray(edges[a][1:])
         per_axis.append(lo[:, None] + (hi - lo)[:, None] * t[None, :])  # [n_a, 4]
-    for iz in range(nn[2]):
-        for iy in range(nn[1]):
-            for ix in range(nn[0]):
-                e = _elem_index(ix, iy, iz, nn)
-                for q in range(NP):
-                    i, j, k = q % 4, (q // 4) % 4, q // 16
-                    idx = (ix, iy, iz)
-                    loc = (i, j, k)
-                    for a in range(dim):
-                        out[e, q, a] = per_axis[a][idx[a], loc[a]]
+    iz, iy, ix = np.meshgrid(np.arange(nn[2]), np.arange(nn[1]), np.arange(nn[0]), indexing="ij")
+    idx = [ix.ravel(), iy.ravel(), iz.ravel()]
+    NP = 4 ** dim
+    q = np.arange(NP)
+    loc = [q % 4, (q // 4) % 4, q // 16]
+    out = np.empty((int(np.prod(n)), NP, dim))
+    for a in range(dim):
+        out[:, :, a] = per_axis[a][idx[a][:, None], loc[a][None, :]]
     return out
 
 
@@ -383,6 +378,40 @@ def small_box_2d(n=8, seed=0, R=2, E=(6, 3), order=3, ic="vortex", surface="es_r
     dt = 0.2 * hmin.min() / (2 * N_POLY + 1) / 2.5
     return Workload(f"box2d_{n}", 2, "euler2d", coords, faces, part, list(E), order, to_soa(u0), dt,
                     "ec_ranocha", surface)
+
+
+def batched_2d(n_inst=256, seed=1, n_min=16, n_max=128, S=12, order=3):
+    """Independent 2D Euler instances: sizes n x n with n ~ U{n_min..n_max},
+    2-4 partitions from a refinement band of seeded position and width (tensor
+    mesh graded in y around the band, partition by shortest edge), and an
+    isentropic vortex or a Kelvin-Helmholtz state by a seeded coin flip.  All
+    members use the same P-ERK family size S (order 3)."""
+    rng = np.random.default_rng(BASE_SEED + 5 + 1000 * seed)
+    E_by_R = {2: [S, 6], 3: [S, 6, 3], 4: [S, 8, 5, 3]}
+    out = []
+    for k in range(n_inst):
+        n = int(rng.integers(n_min, n_max + 1))
+        R = int(rng.integers(2, 5))
+        L = 5.0
+        centre = float(rng.uniform(-0.5 * L, 0.5 * L))
+        per_level = max(1, n // 32)
+        ex = np.linspace(-L, L, n + 1)
+        ey, _, _ = graded_edges(n, -L, L, [centre], R, {l: per_level for l in range(1, R)})
+        coords = tensor_coords([ex, ey])
+        faces = structured_faces([n, n])
+        hmin = min_corner_edge(coords, 2)
+        part = levels_from_h(hmin, 2 * L / n, R)
+        if rng.uniform() < 0.5:
+            u0 = isentropic_vortex(coords[:, :, 0], coords[:, :, 1], 0.0, rng.uniform(-1, 1, 2), float(rng.uniform(3, 5)),
+                                   L=L, R=1.0)
+            ic = "vortex"
+        else:
+            u0 = kelvin_helmholtz(coords[:, :, 0] / L, coords[:, :, 1] / L, phase=float(rng.uniform(0, 2 * math.pi)))
+            ic = "khi"
+        dt = 0.3 * hmin.min() / (2 * N_POLY + 1) / 2.5
+        out.append(Workload(f"batch{k}_{ic}_{n}x{n}_R{R}", 2, "euler2d", coords, faces, part, list(E_by_R[R]), order,
+                            to_soa(u0), dt, "ec_ranocha", "es_rusanov", info=dict(n=n, R=R, ic=ic)))
+    return out
 
 
 def by_name(name, **kw):
