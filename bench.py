@@ -193,7 +193,7 @@ def run_reference(args):
     val = units / el
     sample = (f"{args.steps} oracle steps, each of one instance in turn (numpy float64, one host thread), "
               f"after {args.warmup} warm-up steps")
-    line = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+    line = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": f"{args.workload}: {desc}"},
@@ -243,6 +243,14 @@ def run_native(args):
     big_l2 = dof * 8 > 4 * 135 * 2 ** 20
     l2_flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
+    def ranged(name, fn):
+        # an NVTX range around the launches, so a profiler can select them (ncu --nvtx --nvtx-include)
+        def run():
+            torch.cuda.nvtx.range_push(name)
+            fn()
+            torch.cuda.nvtx.range_pop()
+        return run
+
     def timed(fn, nsteps):
         evs = []
         for _ in range(nsteps):
@@ -265,7 +273,7 @@ def run_native(args):
     clocks.start()
     barrier(world)
     torch.cuda.synchronize()
-    t_chosen = timed(lambda: pk.perrk_step(chosen.h, 1, info=False, stream=sh), args.steps)
+    t_chosen = timed(ranged("chosen_step", lambda: pk.perrk_step(chosen.h, 1, info=False, stream=sh)), args.steps)
     torch.cuda.synchronize()
     barrier(world)
     clk = clocks.stop()
@@ -303,7 +311,7 @@ def run_native(args):
 
     # ---- dominant kernel: an all-active stage of the chosen form, timed live on the launching stream
     st = pk.perrk_stage_info(chosen.h, S - 1)
-    k_s = timed(lambda: pk.perrk_launch_stage(chosen.h, S - 1, stream=sh), 20) / 20
+    k_s = timed(ranged("stage_all_active", lambda: pk.perrk_launch_stage(chosen.h, S - 1, stream=sh)), 20) / 20
     peak, peak_src = measured_peaks()
     achieved = st["bytes"] / k_s / 1e9
 
