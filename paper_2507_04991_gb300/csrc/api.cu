@@ -54,7 +54,7 @@ static perrk_status upload(T *&dst, const std::vector<T> &src, const char *what)
 }
 
 static void free_ctx(Ctx &c) {
-    void *ptrs[] = {c.U, c.K1, c.Ka, c.Kb, c.d, c.Uf, c.K1f, c.Kaf, c.Kbf, c.e_dh, c.g_node, c.g_elem, c.g_fnorm, c.g_wJ, c.g_nbr, c.g_gp,
+    void *ptrs[] = {c.U, c.K1, c.Ka, c.Kb, c.d, c.Uf, c.Ul, c.dh, c.dl, c.e_dhf, c.g_wJ_lo, c.K1f, c.Kaf, c.Kbf, c.e_dh, c.g_node, c.g_elem, c.g_fnorm, c.g_wJ, c.g_nbr, c.g_gp,
                     c.g_elist, c.g_chunk_inst, c.g_chunk_e0, c.g_chunk_e1, c.g_inst_chunk0, c.g_inst_nchunks,
                     c.g_coef, c.g_coef_f, c.g_scal, c.g_partials, c.g_counters, c.g_flags, c.g_records, c.g_mlp,
                     c.g_dftab, c.g_node_f, c.g_elem_f, c.g_fnorm_f, c.g_wJ_f};
@@ -87,20 +87,26 @@ static perrk_status alloc_ctx(Ctx &c) {
     const bool mixed = c.opt.precision == PERRK_MIXED;
     // float64: U, K_1, two stage registers, d; mixed: float64 U and d, FP32 copy of
     // U_n and FP32 stage registers (K is an FP32 result in that form)
-    std::vector<double **> dbufs = {&c.U, &c.d};
-    if (!mixed) dbufs.insert(dbufs.end(), {&c.K1, &c.Ka, &c.Kb});
+    // float64 form: U, K_1, two stage registers, d.  Mixed form: U and d as
+    // float pairs (hi, lo), FP32 stage registers, U (float64) as the staging
+    // buffer of set_state / get_state.
+    std::vector<double **> dbufs = {&c.U};
+    if (!mixed) dbufs.insert(dbufs.end(), {&c.d, &c.K1, &c.Ka, &c.Kb});
     for (double **b : dbufs) {
         PERRK_CUDA(cudaMalloc((void **)b, nstate * sizeof(double)), "state alloc");
         PERRK_CUDA(cudaMemset(*b, 0, nstate * sizeof(double)), "state clear");
     }
     if (mixed) {
-        for (float **b : {&c.Uf, &c.K1f, &c.Kaf, &c.Kbf}) {
+        for (float **b : {&c.Uf, &c.Ul, &c.dh, &c.dl, &c.K1f, &c.Kaf, &c.Kbf}) {
             PERRK_CUDA(cudaMalloc((void **)b, nstate * sizeof(float)), "state alloc");
             PERRK_CUDA(cudaMemset(*b, 0, nstate * sizeof(float)), "state clear");
         }
+        PERRK_CUDA(cudaMalloc((void **)&c.e_dhf, (size_t)c.n_elem * 2 * sizeof(float)), "e_dh alloc");
+        PERRK_CUDA(cudaMemset(c.e_dhf, 0, (size_t)c.n_elem * 2 * sizeof(float)), "e_dh clear");
+    } else {
+        PERRK_CUDA(cudaMalloc((void **)&c.e_dh, (size_t)c.n_elem * sizeof(double)), "e_dh alloc");
+        PERRK_CUDA(cudaMemset(c.e_dh, 0, (size_t)c.n_elem * sizeof(double)), "e_dh clear");
     }
-    PERRK_CUDA(cudaMalloc((void **)&c.e_dh, (size_t)c.n_elem * sizeof(double)), "e_dh alloc");
-    PERRK_CUDA(cudaMemset(c.e_dh, 0, (size_t)c.n_elem * sizeof(double)), "e_dh clear");
     PERRK_TRY(upload(c.g_node, c.geo_node, "geometry"));
     PERRK_TRY(upload(c.g_elem, c.geo_elem, "geometry"));
     PERRK_TRY(upload(c.g_fnorm, c.fnorm, "normals"));
@@ -111,6 +117,9 @@ static perrk_status alloc_ctx(Ctx &c) {
         PERRK_TRY(upload(c.g_elem_f, tof(c.geo_elem), "geometry"));
         PERRK_TRY(upload(c.g_fnorm_f, tof(c.fnorm), "normals"));
         PERRK_TRY(upload(c.g_wJ_f, tof(c.wJ), "weights"));
+        std::vector<float> wlo(c.wJ.size());
+        for (size_t i = 0; i < wlo.size(); ++i) wlo[i] = (float)(c.wJ[i] - (double)(float)c.wJ[i]);
+        PERRK_TRY(upload(c.g_wJ_lo, wlo, "weights"));
     }
     PERRK_TRY(upload(c.g_nbr, c.nbr, "neighbours"));
     PERRK_TRY(upload(c.g_gp, c.gp_of_elem, "partitions"));
@@ -235,7 +244,7 @@ perrk_status perrk_set_state(perrk_ctx *h, const double *u, int on_device, void 
     PERRK_CUDA(cudaMemcpyAsync(c.U, u, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st),
                "set_state copy");
     PERRK_CUDA(cudaMemsetAsync(c.g_flags, 0, sizeof(uint32_t), st), "flags clear");
-    if (c.Uf) PERRK_TRY(launch_convert(c.U, c.Uf, nullptr, nullptr, (size_t)c.V * c.n_elem * c.NP, st));
+    if (c.Uf) PERRK_TRY(launch_split(c.U, c.Uf, c.Ul, (size_t)c.V * c.n_elem * c.NP, st));
     PERRK_TRY(launch_entropy_set(c, st));
     h->host_steps = 0;
     if (!on_device) PERRK_CUDA(cudaStreamSynchronize(st), "set_state sync");
@@ -247,6 +256,7 @@ perrk_status perrk_get_state(perrk_ctx *h, double *u, int on_device, void *strea
     Ctx &c = h->c;
     const size_t bytes = (size_t)c.V * c.n_elem * c.NP * sizeof(double);
     cudaStream_t st = (cudaStream_t)stream;
+    if (c.Uf) PERRK_TRY(launch_join(c.Uf, c.Ul, c.U, (size_t)c.V * c.n_elem * c.NP, st));
     PERRK_CUDA(cudaMemcpyAsync(u, c.U, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st),
                "get_state copy");
     if (!on_device) PERRK_CUDA(cudaStreamSynchronize(st), "get_state sync");

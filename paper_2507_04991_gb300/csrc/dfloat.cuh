@@ -71,6 +71,9 @@ __device__ __forceinline__ df df_div(df x, df y) {
     return df_fast(q1, q2);
 }
 
+// x + y f (df plus df times float)
+__device__ __forceinline__ df df_fma_f(df x, df y, float f) { return df_add(x, df_mul_f(y, f)); }
+
 // float64 -> df (one FP64 subtraction) and back (one FP64 addition).
 __device__ __forceinline__ df df_from(double d) {
     const float hi = __double2float_rn(d);

@@ -24,7 +24,10 @@ namespace perrk {
 
 struct RelaxParams {
     double *U;
-    float *Uf;             // mixed form: FP32 copy of the state, refreshed by the update
+    float *Uf, *Ul;        // mixed form: the state as a float pair U = Uf + Ul
+    const float *dh, *dl;  // mixed form: the direction as a float pair
+    const float *e_dhf;    // mixed form: element Delta H sums as float pairs [n_elem][2]
+    const float *wJf, *wJl;  // mixed form: omega J as a float pair
     const double *d, *e_dh, *wJ;
     const int32_t *chunk_inst, *chunk_e0, *chunk_e1, *inst_chunk0, *inst_nchunks;
     InstScalars *scal;
@@ -42,21 +45,16 @@ struct RelaxParams {
     DfConst K;
 };
 
-// Entropy of one node in double-float (mixed form): returns s and, when
-// dv != nullptr, the float value of <w(u), dv>.  s = -rho (log p - gamma log rho).
+// Entropy of one node in double-float (mixed form) from the state as float
+// pairs: returns s and, when dv != nullptr (the direction, float), the float
+// value of <w(u), dv>.  s = -rho (log p - gamma log rho).
 template <int DIM, int EQ>
-__device__ __forceinline__ df df_entropy(const double *u, const double *dv, const RelaxParams &P, float &wd,
-                                         uint32_t &bad) {
-    constexpr int V = EQ == EQ_BURGERS ? 1 : DIM + 2;
+__device__ __forceinline__ df df_entropy(const df *x, const float *dv, const RelaxParams &P, float &wd, uint32_t &bad) {
     if constexpr (EQ == EQ_BURGERS) {
-        const df x = df_from(u[0]);
-        df sq = df_mul(x, x);
-        if (dv) wd = x.hi * (float)dv[0];
+        df sq = df_mul(x[0], x[0]);
+        if (dv) wd = x[0].hi * dv[0];
         return df{0.5f * sq.hi, 0.5f * sq.lo};
     } else {
-        df x[V];
-#pragma unroll
-        for (int v = 0; v < V; ++v) x[v] = df_from(u[v]);
         const df ir = df_div(df{1.0f, 0.0f}, x[0]);
         df m2 = df_mul(x[1], x[1]);
 #pragma unroll
@@ -78,8 +76,8 @@ __device__ __forceinline__ df df_entropy(const double *u, const double *dv, cons
             const float w0 = P.K.gam.hi - S.hi - gm1 * ke.hi * ip;
             float md = 0.0f;
 #pragma unroll
-            for (int a = 0; a < DIM; ++a) md = fmaf(x[1 + a].hi, (float)dv[1 + a], md);
-            wd = fmaf(w0, (float)dv[0], gm1 * ip * (md - x[0].hi * (float)dv[DIM + 1]));
+            for (int a = 0; a < DIM; ++a) md = fmaf(x[1 + a].hi, dv[1 + a], md);
+            wd = fmaf(w0, dv[0], gm1 * ip * (md - x[0].hi * dv[DIM + 1]));
         }
         return df_neg(df_mul(x[0], S));
     }
@@ -200,7 +198,8 @@ __global__ void k_relax_init(const RelaxParams P) {
         // mixed form: Delta H carries FP32 rounding; double-float block sum on the FP32 pipe
         df r = {0.0f, 0.0f};
         float g = 0.0f, a = 0.0f;
-        for (int e = P.chunk_e0[chunk] + threadIdx.x; e < P.chunk_e1[chunk]; e += blockDim.x) r = df_add(r, df_from(P.e_dh[e]));
+        for (int e = P.chunk_e0[chunk] + threadIdx.x; e < P.chunk_e1[chunk]; e += blockDim.x)
+            r = df_add(r, df{P.e_dhf[2 * e], P.e_dhf[2 * e + 1]});
         block_sum_df(r, g, a);
         s[0] = (double)r.hi;
         c[0] = (double)r.lo;
@@ -251,18 +250,23 @@ __global__ void __launch_bounds__(256) k_newton_pass(const RelaxParams P) {
     double s[3] = {0, 0, 0}, c[3] = {0, 0, 0}, tot[3];
     uint32_t bad = 0;
     if constexpr (DF) {
+        // U_n + gamma dt d and the entropy in double-float on the FP32 pipe
+        const df gdtf = df_from(gdt);
         df R = {0.0f, 0.0f};
         float G = 0.0f, A = 0.0f;
         for (size_t j = n0 + threadIdx.x; j < n1; j += blockDim.x) {
-            double u[V], dv[V];
+            df x[V];
+            float dv[V];
 #pragma unroll
             for (int v = 0; v < V; ++v) {
-                dv[v] = __ldg(P.d + v * NPtot + j);
-                u[v] = fma(gdt, dv[v], __ldg(P.U + v * NPtot + j));
+                const size_t i = v * NPtot + j;
+                const df dd{__ldg(P.dh + i), __ldg(P.dl + i)};
+                dv[v] = dd.hi;
+                x[v] = df_add(df{__ldg(P.Uf + i), __ldg(P.Ul + i)}, df_mul(gdtf, dd));
             }
             float wd;
-            const df sv = df_entropy<DIM, EQ>(u, dv, P, wd, bad);
-            const df wj = df_from(__ldg(P.wJ + j));
+            const df sv = df_entropy<DIM, EQ>(x, dv, P, wd, bad);
+            const df wj{__ldg(P.wJf + j), __ldg(P.wJl + j)};
             R = df_add(R, df_mul(sv, wj));
             G = fmaf(wj.hi, wd, G);
             A = fmaf(wj.hi, fabsf(sv.hi), A);
@@ -346,34 +350,44 @@ __global__ void __launch_bounds__(256) k_update(const RelaxParams P) {
     uint32_t bad = 0;
     df R = {0.0f, 0.0f};
     float A = 0.0f, G = 0.0f;
+    const df gdtf = df_from(gdt);
     for (size_t j = n0 + threadIdx.x; j < n1; j += blockDim.x) {
+        if constexpr (DF) {
+            // U_{n+1} = U_n + gamma dt d in double-float (FP32 pipe)
+            df x[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const size_t i = v * NPtot + j;
+                x[v] = df_add(df{P.Uf[i], P.Ul[i]}, df_mul(gdtf, df{__ldg(P.dh + i), __ldg(P.dl + i)}));
+                P.Uf[i] = x[v].hi;
+                P.Ul[i] = x[v].lo;
+                if (!isfinite(x[v].hi)) bad |= PERRK_FLAG_NONFINITE;
+            }
+            if (needH) {
+                float wd;
+                const df sv = df_entropy<DIM, EQ>(x, nullptr, P, wd, bad);
+                const df t = df_mul(sv, df{__ldg(P.wJf + j), __ldg(P.wJl + j)});
+                R = df_add(R, t);
+                A += fabsf(t.hi);
+            }
+            continue;
+        } else {
         double u[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             u[v] = fma(gdt, __ldg(P.d + v * NPtot + j), P.U[v * NPtot + j]);
             P.U[v * NPtot + j] = u[v];
-            if constexpr (DF) {
-                const float uf = __double2float_rn(u[v]);
-                P.Uf[v * NPtot + j] = uf;
-                if (!isfinite(uf)) bad |= PERRK_FLAG_NONFINITE;
-            } else {
-                if (!isfinite(u[v])) bad |= PERRK_FLAG_NONFINITE;
-            }
+            if (!isfinite(u[v])) bad |= PERRK_FLAG_NONFINITE;
         }
         if (needH) {
-            if constexpr (DF) {
-                float wd;
-                const df sv = df_entropy<DIM, EQ>(u, nullptr, P, wd, bad);
-                const df t = df_mul(sv, df_from(__ldg(P.wJ + j)));
-                R = df_add(R, t);
-                A += fabsf(t.hi);
-            } else {
+            {
                 double sv;
                 node_entropy<DIM, EQ>(u, P.gamma_gas, sv, nullptr, bad);
                 const double wj = __ldg(P.wJ + j);
                 comp_add(s[0], c[0], wj * sv);
                 comp_add(s[1], c[1], wj * fabs(sv));
             }
+        }
         }
     }
     if (bad) atomicOr(P.flags, bad);
@@ -455,16 +469,19 @@ __global__ void __launch_bounds__(256) k_entropy(const RelaxParams P) {
     df R = {0.0f, 0.0f};
     float A = 0.0f, G = 0.0f;
     for (size_t j = n0 + threadIdx.x; j < n1; j += blockDim.x) {
-        double u[V];
-#pragma unroll
-        for (int v = 0; v < V; ++v) u[v] = __ldg(P.U + v * NPtot + j);
         if constexpr (DF) {
+            df x[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) x[v] = df{__ldg(P.Uf + v * NPtot + j), __ldg(P.Ul + v * NPtot + j)};
             float wd;
-            const df sv = df_entropy<DIM, EQ>(u, nullptr, P, wd, bad);
-            const df t = df_mul(sv, df_from(__ldg(P.wJ + j)));
+            const df sv = df_entropy<DIM, EQ>(x, nullptr, P, wd, bad);
+            const df t = df_mul(sv, df{__ldg(P.wJf + j), __ldg(P.wJl + j)});
             R = df_add(R, t);
             A += fabsf(t.hi);
         } else {
+            double u[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) u[v] = __ldg(P.U + v * NPtot + j);
             double sv;
             node_entropy<DIM, EQ>(u, P.gamma_gas, sv, nullptr, bad);
             const double wj = __ldg(P.wJ + j);
@@ -505,6 +522,12 @@ static RelaxParams relax_params(Ctx &c) {
     RelaxParams P{};
     P.U = c.U;
     P.Uf = c.Uf;
+    P.Ul = c.Ul;
+    P.dh = c.dh;
+    P.dl = c.dl;
+    P.e_dhf = c.e_dhf;
+    P.wJf = c.g_wJ_f;
+    P.wJl = c.g_wJ_lo;
     P.d = c.d;
     P.e_dh = c.e_dh;
     P.wJ = c.g_wJ;

@@ -32,9 +32,15 @@ struct StageCoef {
     double first_b;  // 1.0 at the instance's first stage with b != 0
 };
 
+// FP32 twin for the mixed form; b_i as a float pair (b_hi + b_lo) for the
+// double-float direction d += b_i K_i.
 struct StageCoefF {
     float a1;
     float asub;
+    float b_hi;
+    float b_lo;
+    int32_t has_b;    // b_i != 0
+    int32_t first_b;  // first stage of the instance with b_i != 0
 };
 
 // Per-instance relaxation scalars, resident in device memory.
@@ -107,9 +113,15 @@ struct Ctx {
     // device buffers
     double *U = nullptr, *K1 = nullptr, *Ka = nullptr, *Kb = nullptr, *d = nullptr;
     float *Uf = nullptr, *K1f = nullptr, *Kaf = nullptr, *Kbf = nullptr;   // mixed form
+    // mixed form: the state and the direction as float pairs, U = Uf + Ul and
+    // d = dh + dl (double-float, ~48 bits); U (float64) is then only the
+    // staging buffer of set_state / get_state
+    float *Ul = nullptr, *dh = nullptr, *dl = nullptr;
     double *e_dh = nullptr;                   // [n_elem] per-element b-weighted <w, K> sums
+    float *e_dhf = nullptr;                   // mixed form: the same as float pairs [n_elem][2]
     double *g_node = nullptr, *g_elem = nullptr, *g_fnorm = nullptr, *g_wJ = nullptr;
     float *g_node_f = nullptr, *g_elem_f = nullptr, *g_fnorm_f = nullptr, *g_wJ_f = nullptr;
+    float *g_wJ_lo = nullptr;                 // mixed form: omega J = g_wJ_f + g_wJ_lo
     int32_t *g_nbr = nullptr, *g_gp = nullptr, *g_elist = nullptr;
     int32_t *g_chunk_inst = nullptr, *g_chunk_e0 = nullptr, *g_chunk_e1 = nullptr;
     int32_t *g_inst_chunk0 = nullptr, *g_inst_nchunks = nullptr;
@@ -153,6 +165,9 @@ perrk_status launch_stage(Ctx &c, int stage, bool rhs_only, const double *in_u, 
                           float *out_kf, void *stream);
 perrk_status launch_convert(const double *src_d, float *dst_f, const float *src_f, double *dst_d, size_t n,
                             void *stream);
+// float64 <-> float pair (hi = round(x), lo = round(x - hi)); join: hi + lo
+perrk_status launch_split(const double *src, float *hi, float *lo, size_t n, void *stream);
+perrk_status launch_join(const float *hi, const float *lo, double *dst, size_t n, void *stream);
 perrk_status launch_relax_init(Ctx &c, void *stream);
 perrk_status launch_newton_pass(Ctx &c, void *stream);
 perrk_status launch_update(Ctx &c, int rec_slot, void *stream);

@@ -57,6 +57,20 @@ __device__ __forceinline__ Real ln_mean(Real x, Real y, Real lx, Real ly) {
     return d * rcp(ly - lx);
 }
 
+// FP32 (mixed form): both branches are computed and one is selected, so the
+// warp does not diverge on the branch test (the unused direct quotient may be
+// inf or NaN when x == y; it is discarded).
+template <>
+__device__ __forceinline__ float ln_mean<float>(float x, float y, float lx, float ly) {
+    const float d = y - x, s = y + x;
+    const float f = d * rcp(s);
+    const float u = f * f;
+    const float poly = fmaf(u, fmaf(u, fmaf(u, -44.0f / 945.0f, -4.0f / 45.0f), -1.0f / 3.0f), 1.0f);
+    const float series = 0.5f * s * poly;
+    const float direct = d * rcp(ly - lx);
+    return u < Lit<float>::series_u ? series : direct;
+}
+
 // 1 / ln_mean(x, y): (x + y)^-1 * 2 atanh(f)/f = 2/(x+y) (1 + u/3 + u^2/5 + u^3/7 + ...)
 template <typename Real>
 __device__ __forceinline__ Real inv_ln_mean(Real x, Real y, Real lx, Real ly) {
@@ -69,6 +83,18 @@ __device__ __forceinline__ Real inv_ln_mean(Real x, Real y, Real lx, Real ly) {
         return Real(2.0) * rs * poly;
     }
     return (ly - lx) * rcp(d);
+}
+
+template <>
+__device__ __forceinline__ float inv_ln_mean<float>(float x, float y, float lx, float ly) {
+    const float d = y - x, s = y + x;
+    const float rs = rcp(s);
+    const float f = d * rs;
+    const float u = f * f;
+    const float poly = fmaf(u, fmaf(u, fmaf(u, 1.0f / 7.0f, 1.0f / 5.0f), 1.0f / 3.0f), 1.0f);
+    const float series = 2.0f * rs * poly;
+    const float direct = (ly - lx) * rcp(d);
+    return u < Lit<float>::series_u ? series : direct;
 }
 
 // Per-node primitive bundle used by Ranocha's flux.
@@ -164,6 +190,21 @@ __device__ __forceinline__ Real max_speed(const Prim<Real, DIM> &L, const Prim<R
             nn = dfma(n[a], n[a], nn);
         }
         nn = dsqrt(nn);
+    }
+    Real cl = dsqrt(gam * L.p * rcp(L.rho)), cr = dsqrt(gam * R.p * rcp(R.rho));
+    Real a = dfma(cl, nn, fabs(vnl)), b = dfma(cr, nn, fabs(vnr));
+    return a > b ? a : b;
+}
+
+// max wave speed with the normal's length given (box elements: |n| is the
+// metric factor itself, no square root)
+template <typename Real, int DIM>
+__device__ __forceinline__ Real max_speed_nn(const Prim<Real, DIM> &L, const Prim<Real, DIM> &R, const Real *n, Real nn,
+                                             Real gam) {
+    Real vnl = 0, vnr = 0;
+    for (int a = 0; a < DIM; ++a) {
+        vnl = dfma(L.v[a], n[a], vnl);
+        vnr = dfma(R.v[a], n[a], vnr);
     }
     Real cl = dsqrt(gam * L.p * rcp(L.rho)), cr = dsqrt(gam * R.p * rcp(R.rho));
     Real a = dfma(cl, nn, fabs(vnl)), b = dfma(cr, nn, fabs(vnr));

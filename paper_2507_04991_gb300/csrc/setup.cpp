@@ -403,7 +403,7 @@ void make_chunks(Ctx &c, int sm_count) {
 
 void stage_coefficients(const Ctx &c, std::vector<StageCoef> &coef, std::vector<StageCoefF> &coef_f) {
     coef.assign((size_t)c.S * c.n_gp, StageCoef{0, 0, 0, 0});
-    coef_f.assign((size_t)c.S * c.n_gp, StageCoefF{0, 0});
+    coef_f.assign((size_t)c.S * c.n_gp, StageCoefF{0, 0, 0, 0, 0, 0});
     for (const Instance &I : c.inst) {
         int first_b = -1;
         for (int j = 0; j < I.S; ++j)
@@ -421,7 +421,10 @@ void stage_coefficients(const Ctx &c, std::vector<StageCoef> &coef, std::vector<
                 sc.asub = I.dt * I.asub[r * I.S + j];
                 sc.b = I.b[j];
                 sc.first_b = (j == first_b) ? 1.0 : 0.0;
-                coef_f[(size_t)i * c.n_gp + I.gp0 + r] = StageCoefF{(float)sc.a1, (float)sc.asub};
+                const float b_hi = (float)sc.b;
+                const float b_lo = (float)(sc.b - (double)b_hi);
+                coef_f[(size_t)i * c.n_gp + I.gp0 + r] =
+                    StageCoefF{(float)sc.a1, (float)sc.asub, b_hi, b_lo, sc.b != 0.0 ? 1 : 0, j == first_b ? 1 : 0};
             }
         }
     }

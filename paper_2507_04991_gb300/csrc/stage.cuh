@@ -16,6 +16,7 @@
 // the '+' side), so both elements compute bit-identical values.
 #pragma once
 
+#include "dfloat.cuh"
 #include "physics.cuh"
 
 namespace perrk {
@@ -26,6 +27,7 @@ struct StageParams {
     const float *Uf, *K1f, *Kprevf;            // mixed form: FP32 copy of U_n, FP32 stage registers
     float *Koutf;
     double *d, *e_dh;
+    float *dh, *dl, *e_dhf;                    // mixed form: d and the element Delta H sums as float pairs
     const int32_t *elist, *nbr, *gp;
     const StageCoef *coef;      // [n_gp] rows of this stage
     const StageCoefF *coef_f;
@@ -150,6 +152,7 @@ __global__ void __launch_bounds__(EPB * ipow4(DIM)) k_stage(const StageParams P)
     constexpr int NPAIR = NLINE * 6;                  // node pairs (q < m) on those lines
     __shared__ Real s_pf[EPB][NPAIR][V];              // two-point volume fluxes, one per pair
 
+    constexpr bool MIX = sizeof(Real) == 4;           // mixed form: no float64 instruction per node
     const int el = threadIdx.x / NP, q = threadIdx.x % NP;
     const size_t NPtot = P.NE * NP;
     Real gm1, inv_gm1, gam, inv_w;
@@ -260,7 +263,26 @@ __global__ void __launch_bounds__(EPB * ipow4(DIM)) k_stage(const StageParams P)
                 const Prim<Real, DD> &PL = self_plus ? ps : pn;
                 const Prim<Real, DD> &PR = self_plus ? pn : ps;
                 const int k = f >> 1;
-                if constexpr (CURVED) {
+                if constexpr (MIX && !CURVED) {
+                    // axis normal as a full vector (zeros off the axis): one
+                    // instruction stream for every face direction
+                    Real nv[DD];
+#pragma unroll
+                    for (int a = 0; a < DD; ++a) nv[a] = (a == k) ? nrm[0] : Real(0);
+                    ranocha<Real, DD, -1>(PL, PR, nv, inv_gm1, fs);
+                    if (P.es) {
+                        Real lam = max_speed_nn<Real, DD>(PL, PR, nv, fabs(nrm[0]), gam);
+#pragma unroll
+                        for (int v = 0; v < V; ++v) fs[v] -= Real(0.5) * lam * (uR[v] - uL[v]);
+                    }
+                } else if constexpr (MIX) {
+                    ranocha<Real, DD, -1>(PL, PR, nrm, inv_gm1, fs);
+                    if (P.es) {
+                        Real lam = max_speed<Real, DD, -1>(PL, PR, nrm, gam);
+#pragma unroll
+                        for (int v = 0; v < V; ++v) fs[v] -= Real(0.5) * lam * (uR[v] - uL[v]);
+                    }
+                } else if constexpr (CURVED) {
                     ranocha<Real, DD, -1>(PL, PR, nrm, inv_gm1, fs);
                     euler_flux<Real, DD, -1>(us, ps, nrm, fp);
                     if (P.es) {
@@ -285,8 +307,16 @@ __global__ void __launch_bounds__(EPB * ipow4(DIM)) k_stage(const StageParams P)
                 }
             }
             const Real sg = self_plus ? Real(1) : Real(-1);
+            if constexpr (MIX) {
+                // LGL SBP: 2 D_NN = 1/omega_N and 2 D_00 = -1/omega_0, so the
+                // diagonal volume term 2 D_qq f(U_q).Ja and the -f(U_q).nu part
+                // of the lift cancel at end nodes; only f* remains
 #pragma unroll
-            for (int v = 0; v < V; ++v) s_sf[el][sl][v] = sg * (fs[v] - fp[v]) * inv_w;
+                for (int v = 0; v < V; ++v) s_sf[el][sl][v] = sg * fs[v] * inv_w;
+            } else {
+#pragma unroll
+                for (int v = 0; v < V; ++v) s_sf[el][sl][v] = sg * (fs[v] - fp[v]) * inv_w;
+            }
         }
 
         // ---- C: volume flux differencing.  The two-point flux is symmetric,
@@ -336,6 +366,13 @@ __global__ void __launch_bounds__(EPB * ipow4(DIM)) k_stage(const StageParams P)
                     nv[0] = Real(0.5) * (s_ja[el][2 * k][qa] + s_ja[el][2 * k][qb]);
                     nv[1 % DD] = Real(0.5) * (s_ja[el][2 * k + 1][qa] + s_ja[el][2 * k + 1][qb]);
                     ranocha<Real, DD, -1>(pa, pb, nv, inv_gm1, F);
+                } else if constexpr (MIX) {
+                    Real jk = Jak_box[0];
+#pragma unroll
+                    for (int a = 1; a < DD; ++a) jk = (k == a) ? Jak_box[a] : jk;
+#pragma unroll
+                    for (int a = 0; a < DD; ++a) nv[a] = (a == k) ? jk : Real(0);
+                    ranocha<Real, DD, -1>(pa, pb, nv, inv_gm1, F);
                 } else {
                     nv[0] = Jak_box[k];
                     if (k == 0) ranocha<Real, DD, 0>(pa, pb, nv, inv_gm1, F);
@@ -366,8 +403,9 @@ __global__ void __launch_bounds__(EPB * ipow4(DIM)) k_stage(const StageParams P)
 #pragma unroll
                 for (int v = 0; v < V; ++v) acc[v] = dfma(Dv, s_pf[el][base + lp][v], acc[v]);
             }
-            if (ik == 0 || ik == 3) {
-                // diagonal term 2 D_qq f(U_q) . Ja^k_q (consistency of the two-point flux)
+            if (!MIX && (ik == 0 || ik == 3)) {
+                // diagonal term 2 D_qq f(U_q) . Ja^k_q (consistency of the two-point flux);
+                // the mixed form folds it into the lift (see phase B)
                 const Real Dv = Real(2.0) * Geo<Real>::D(P, ik * 4 + ik);
                 Real F[V];
                 if constexpr (EQ == EQ_BURGERS) {
@@ -420,29 +458,16 @@ __global__ void __launch_bounds__(EPB * ipow4(DIM)) k_stage(const StageParams P)
         }
 
         // ---- E: stages with b_i != 0: entropy integrand and direction
-        if (P.do_b) {
-            const StageCoef c = P.coef[g];
-            double wdot = 0.0;
-            if (c.b != 0.0) {
-                if constexpr (sizeof(Real) == 8) {
-                    double Ui[V];
-#pragma unroll
-                    for (int v = 0; v < V; ++v) Ui[v] = P.stage1 ? Ud[v] : fma(c.asub, Kpd[v], fma(c.a1, K1d[v], Ud[v]));
-                    if constexpr (EQ == EQ_BURGERS) {
-                        wdot = Ui[0] * (double)Kr[0];
-                    } else {
-                        constexpr int DD = EQ == EQ_EULER ? DIM : 1;
-                        double s, w[DD + 2];
-                        euler_entropy<DD>(Ui, P.gamma_gas, s, w, bad);
-#pragma unroll
-                        for (int v = 0; v < V; ++v) wdot = fma(w[v], (double)Kr[v], wdot);
-                    }
-                } else {
-                    // Mixed form: K_i carries FP32 rounding, so the integrand
-                    // <w(U_{n,i}), K_i> is evaluated from the FP32 stage state
-                    // and primitives (log p = log rho - log beta: no extra
-                    // logs); the per-element and global sums stay float64.
-                    Real wdf = 0;
+        if constexpr (MIX) {
+            if (P.do_b) {
+                // Mixed form, FP32 pipe only: K_i carries FP32 rounding, so the
+                // integrand <w(U_{n,i}), K_i> is evaluated from the FP32 stage
+                // state and primitives (log p = log rho - log beta: no extra
+                // logs) and summed over the element in FP32; the direction
+                // d += b_i K_i and the element's running sum are float pairs.
+                const StageCoefF cf = P.coef_f[g];
+                float wdf = 0.0f;
+                if (cf.has_b) {
                     if constexpr (EQ == EQ_BURGERS) {
                         wdf = u[0] * Kr[0];
                     } else {
@@ -463,9 +488,53 @@ __global__ void __launch_bounds__(EPB * ipow4(DIM)) k_stage(const StageParams P)
                         // w_m . K_m + w_E K_E = (gamma-1) rho / p (v . K_m - K_E)
                         wdf = dfma(w0, k0, gm1 * rho * ip * (mk - kE));
                     }
-                    wdot = (double)(wdf * __ldg(P.wJ_f + idx));
+                    wdf *= __ldg(P.wJ_f + idx);
+                    if (valid) {
+                        const df bb{cf.b_hi, cf.b_lo};
+#pragma unroll
+                        for (int v = 0; v < V; ++v) {
+                            const size_t j = v * NPtot + idx;
+                            const df dn = cf.first_b ? df_mul_f(bb, Kr[v]) : df_fma_f(df{P.dh[j], P.dl[j]}, bb, Kr[v]);
+                            P.dh[j] = dn.hi;
+                            P.dl[j] = dn.lo;
+                        }
+                    }
                 }
-                if constexpr (sizeof(Real) == 8) wdot *= __ldg(P.wJ + idx);
+                // element sum over its NP consecutive threads (fixed shuffle tree)
+                constexpr int W = NP < 32 ? NP : 32;
+#pragma unroll
+                for (int off = W / 2; off > 0; off >>= 1) wdf += __shfl_xor_sync(0xffffffffu, wdf, off);
+                if constexpr (NP > 32) {
+                    float *sr = reinterpret_cast<float *>(&s_red[el][0]);
+                    if ((q & 31) == 0) sr[q >> 5] = wdf;
+                    __syncthreads();
+                    if (q == 0)
+                        for (int w = 1; w < NP / 32; ++w) wdf += sr[w];
+                }
+                if (q == 0 && valid && cf.has_b) {
+                    const df bs = df_mul_f(df{cf.b_hi, cf.b_lo}, wdf);
+                    const df en = cf.first_b ? bs : df_add(df{P.e_dhf[2 * e], P.e_dhf[2 * e + 1]}, bs);
+                    P.e_dhf[2 * e] = en.hi;
+                    P.e_dhf[2 * e + 1] = en.lo;
+                }
+            }
+        } else if (P.do_b) {
+            const StageCoef c = P.coef[g];
+            double wdot = 0.0;
+            if (c.b != 0.0) {
+                double Ui[V];
+#pragma unroll
+                for (int v = 0; v < V; ++v) Ui[v] = P.stage1 ? Ud[v] : fma(c.asub, Kpd[v], fma(c.a1, K1d[v], Ud[v]));
+                if constexpr (EQ == EQ_BURGERS) {
+                    wdot = Ui[0] * (double)Kr[0];
+                } else {
+                    constexpr int DD = EQ == EQ_EULER ? DIM : 1;
+                    double s, w[DD + 2];
+                    euler_entropy<DD>(Ui, P.gamma_gas, s, w, bad);
+#pragma unroll
+                    for (int v = 0; v < V; ++v) wdot = fma(w[v], (double)Kr[v], wdot);
+                }
+                wdot *= __ldg(P.wJ + idx);
                 if (valid) {
 #pragma unroll
                     for (int v = 0; v < V; ++v) {

@@ -28,6 +28,33 @@ perrk_status launch_convert(const double *src_d, float *dst_f, const float *src_
     return cuda_check((int)cudaGetLastError(), "convert launch");
 }
 
+__global__ void k_split(const double *src, float *hi, float *lo, size_t n) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double x = src[i];
+    const float h = __double2float_rn(x);
+    hi[i] = h;
+    lo[i] = __double2float_rn(x - (double)h);
+}
+
+__global__ void k_join(const float *hi, const float *lo, double *dst, size_t n) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    dst[i] = (double)hi[i] + (double)lo[i];
+}
+
+perrk_status launch_split(const double *src, float *hi, float *lo, size_t n, void *stream) {
+    if (n == 0) return PERRK_OK;
+    k_split<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(src, hi, lo, n);
+    return cuda_check((int)cudaGetLastError(), "split launch");
+}
+
+perrk_status launch_join(const float *hi, const float *lo, double *dst, size_t n, void *stream) {
+    if (n == 0) return PERRK_OK;
+    k_join<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(hi, lo, dst, n);
+    return cuda_check((int)cudaGetLastError(), "join launch");
+}
+
 perrk_status launch_stage(Ctx &c, int stage, bool rhs_only, const double *in_u, const float *in_uf, double *out_k,
                           float *out_kf, void *stream) {
     StageParams P{};
@@ -46,6 +73,9 @@ perrk_status launch_stage(Ctx &c, int stage, bool rhs_only, const double *in_u, 
     }
     P.d = c.d;
     P.e_dh = c.e_dh;
+    P.dh = c.dh;
+    P.dl = c.dl;
+    P.e_dhf = c.e_dhf;
     P.elist = c.g_elist;
     P.nbr = c.g_nbr;
     P.gp = c.g_gp;
