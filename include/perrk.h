@@ -176,17 +176,33 @@ perrk_status perrk_set_dt(perrk_ctx *ctx, int inst, double dt);
  * nsteps * n_inst records (step-major), which forces a stream sync. */
 perrk_status perrk_step(perrk_ctx *ctx, int nsteps, perrk_step_info *info, void *stream);
 
-/* Autotune the launch mapping of ctx on the current device: times the
- * all-active stage kernel for every valid elements-per-CTA choice and grid
+/* Autotune the launch mapping of ctx on the current device: times the first
+ * and the last stage kernel for every valid elements-per-CTA choice, grid
  * mapping (one CTA per element group, or a persistent grid of k CTAs per SM)
- * and the relaxation block size, keeps the fastest and re-captures the step
- * graph.  Results do not depend on the mapping (same per-element
- * arithmetic).  Overwrites K_1 (call between steps).  best_ms_out (nullable):
- * time of the chosen stage launch.  Synchronises the stream. */
+ * and, for the mixed form on box elements, stage kernel variant (generic;
+ * float4 box kernel; box kernel staging the next element group with
+ * cp.async), then the relaxation block size; keeps the fastest and
+ * re-captures the step graph.  Results do not depend on the choice (same
+ * per-element arithmetic in the same order).  Overwrites the stage registers
+ * and d (call between steps).  best_ms_out (nullable): mean time of the chosen
+ * stage launches.  Synchronises the stream. */
 perrk_status perrk_autotune(perrk_ctx *ctx, void *stream, float *best_ms_out);
 
-/* Current launch mapping (elements per CTA, persistent grid size or 0, relaxation block size). */
-perrk_status perrk_tuning(const perrk_ctx *ctx, int *elems_per_cta, int *persistent_grid, int *relax_threads);
+/* Current launch mapping (elements per CTA, persistent grid size or 0,
+ * relaxation block size, stage kernel variant 0/1/2 as above); each output
+ * pointer is nullable. */
+perrk_status perrk_tuning(const perrk_ctx *ctx, int *elems_per_cta, int *persistent_grid, int *relax_threads,
+                          int *stage_variant);
+
+/* Set the launch mapping explicitly (reproducible timing, or a mapping found
+ * on another run): elements per CTA (1D: 16, 32; 2D: 4, 8, 16; 3D: 1, 2, 4),
+ * persistent grid size (0: one CTA per element group), relaxation block size
+ * (128, 256), stage kernel variant (0/1/2 for the mixed form on box elements;
+ * other contexts keep theirs).  Values outside these sets: PERRK_INVALID_ARG.
+ * A mapping whose shared memory does not fit is reported by the next launch
+ * (PERRK_CUDA_ERROR, invalid configuration).  The step graph is re-captured. */
+perrk_status perrk_set_tuning(perrk_ctx *ctx, int elems_per_cta, int persistent_grid, int relax_threads,
+                              int stage_variant);
 
 /* H(U) = sum omega J s(U) of the current state per instance (host array [n_inst]); syncs. */
 perrk_status perrk_entropy(perrk_ctx *ctx, double *H, void *stream);

@@ -32,7 +32,7 @@ EXPORTED = [
     "perrk_default_options", "perrk_create", "perrk_create_batched", "perrk_destroy", "perrk_build_tableau",
     "perrk_shape", "perrk_set_state", "perrk_get_state", "perrk_set_dt", "perrk_step", "perrk_entropy",
     "perrk_rhs", "perrk_mlp_size", "perrk_mlp_features", "perrk_set_mlp", "perrk_mlp_train", "perrk_mlp_grad",
-    "perrk_last_error", "perrk_status_string", "perrk_launch_stage", "perrk_stage_info", "perrk_df_log", "perrk_autotune", "perrk_tuning", "perrk_entropy_static",
+    "perrk_last_error", "perrk_status_string", "perrk_launch_stage", "perrk_stage_info", "perrk_df_log", "perrk_autotune", "perrk_tuning", "perrk_set_tuning", "perrk_entropy_static",
 ]
 
 
@@ -99,7 +99,8 @@ def load(path=LIB_PATH):
         "perrk_launch_stage": (I, [P, I, P]),
         "perrk_df_log": (I, [P, P, I, P]),
         "perrk_autotune": (I, [P, P, P]),
-        "perrk_tuning": (I, [P, P, P, P]),
+        "perrk_tuning": (I, [P, P, P, P, P]),
+        "perrk_set_tuning": (I, [P, I, I, I, I]),
         "perrk_entropy_static": (I, [I, D, P, P, C.c_longlong, P, P]),
         "perrk_stage_info": (I, [P, I, P, P, P, P, P]),
         "perrk_status_string": (C.c_char_p, [I]),
@@ -299,10 +300,14 @@ def perrk_autotune(h, stream=0):
     return ms.value
 
 
+def perrk_set_tuning(h, elems_per_cta, persistent_grid=0, relax_threads=128, stage_variant=1):
+    _check(load().perrk_set_tuning(h, elems_per_cta, persistent_grid, relax_threads, stage_variant), "perrk_set_tuning")
+
+
 def perrk_tuning(h):
-    a, b, c = C.c_int(), C.c_int(), C.c_int()
-    _check(load().perrk_tuning(h, C.byref(a), C.byref(b), C.byref(c)), "perrk_tuning")
-    return dict(elems_per_cta=a.value, persistent_grid=b.value, relax_threads=c.value)
+    a, b, c, d = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+    _check(load().perrk_tuning(h, C.byref(a), C.byref(b), C.byref(c), C.byref(d)), "perrk_tuning")
+    return dict(elems_per_cta=a.value, persistent_grid=b.value, relax_threads=c.value, stage_variant=d.value)
 
 
 def perrk_entropy_static(equation, gamma_gas, u_ptr, wJ_ptr, n_nodes, out_ptr, stream=0):

@@ -294,7 +294,11 @@ perrk_status perrk_step(perrk_ctx *h, int nsteps, perrk_step_info *info, void *s
         perrk_status s = enqueue_step(c, h->capture_stream);
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamEndCapture(h->capture_stream, &g);
-        if (s != PERRK_OK) return s;
+        if (s != PERRK_OK) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return s;
+        }
         PERRK_CUDA(e, "capture end");
         cudaGraphExec_t ex = nullptr;
         PERRK_CUDA(cudaGraphInstantiate(&ex, g, 0), "graph instantiate");
@@ -349,37 +353,48 @@ perrk_status perrk_autotune(perrk_ctx *h, void *stream, float *best_ms_out) {
     cudaEvent_t e0, e1;
     PERRK_CUDA(cudaEventCreate(&e0), "event");
     PERRK_CUDA(cudaEventCreate(&e1), "event");
+    // kernel variants: the mixed form on box elements has three stage kernels
+    const bool box = c.opt.precision == PERRK_MIXED && c.equation != PERRK_BURGERS_1D && !c.curved && c.dim >= 2;
+    const std::vector<int> variants = box ? std::vector<int>{0, 1, 2} : std::vector<int>{c.stage_variant};
+    // timed launches: the first stage and the last (usually all elements active)
+    const int stages[2] = {0, c.S - 1};
     float best = 1e30f;
-    int best_epb = c.stage_epb, best_grid = c.stage_persistent;
-    const int save_epb = c.stage_epb, save_grid = c.stage_persistent;
-    for (int epb : epbs)
-        for (int g : grids) {
-            c.stage_epb = epb;
-            c.stage_persistent = g;
-            // warm-up launch; an unsupported configuration reports an error and is skipped
-            if (launch_stage(c, 0, false, nullptr, nullptr, nullptr, nullptr, st) != PERRK_OK) {
-                cudaGetLastError();
-                continue;
+    int best_epb = c.stage_epb, best_grid = c.stage_persistent, best_var = c.stage_variant;
+    const int save_epb = c.stage_epb, save_grid = c.stage_persistent, save_var = c.stage_variant;
+    for (int var : variants)
+        for (int epb : epbs)
+            for (int g : grids) {
+                c.stage_variant = var;
+                c.stage_epb = epb;
+                c.stage_persistent = g;
+                // warm-up launches; an unsupported configuration reports an error and is skipped
+                bool ok = true;
+                for (int si : stages) ok = ok && launch_stage(c, si, false, nullptr, nullptr, nullptr, nullptr, st) == PERRK_OK;
+                if (!ok) {
+                    cudaGetLastError();
+                    continue;
+                }
+                float tot = 0.0f;
+                for (int rep = 0; rep < 3 && ok; ++rep)
+                    for (int si : stages) {
+                        cudaEventRecord(e0, st);
+                        ok = ok && launch_stage(c, si, false, nullptr, nullptr, nullptr, nullptr, st) == PERRK_OK;
+                        cudaEventRecord(e1, st);
+                        cudaEventSynchronize(e1);
+                        float ms = 0.0f;
+                        cudaEventElapsedTime(&ms, e0, e1);
+                        tot += ms;
+                    }
+                if (ok && tot < best) {
+                    best = tot;
+                    best_epb = epb;
+                    best_grid = g;
+                    best_var = var;
+                }
             }
-            float tot = 0.0f;
-            bool ok = true;
-            for (int rep = 0; rep < 3 && ok; ++rep) {
-                cudaEventRecord(e0, st);
-                ok = launch_stage(c, 0, false, nullptr, nullptr, nullptr, nullptr, st) == PERRK_OK;
-                cudaEventRecord(e1, st);
-                cudaEventSynchronize(e1);
-                float ms = 0.0f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                tot += ms;
-            }
-            if (ok && tot < best) {
-                best = tot;
-                best_epb = epb;
-                best_grid = g;
-            }
-        }
     c.stage_epb = best < 1e29f ? best_epb : save_epb;
     c.stage_persistent = best < 1e29f ? best_grid : save_grid;
+    c.stage_variant = best < 1e29f ? best_var : save_var;
     // relaxation block size: time the entropy pass (a full-state float64/double-float pass)
     float best_r = 1e30f;
     int best_t = c.relax_threads;
@@ -402,15 +417,38 @@ perrk_status perrk_autotune(perrk_ctx *h, void *stream, float *best_ms_out) {
     cudaEventDestroy(e1);
     c.tuned = true;
     c.graph_dirty = true;
-    if (best_ms_out) *best_ms_out = best / 3.0f;
+    if (best_ms_out) *best_ms_out = best / 6.0f;
     return cuda_check((int)cudaStreamSynchronize(st), "autotune sync");
 }
 
-perrk_status perrk_tuning(const perrk_ctx *h, int *elems_per_cta, int *persistent_grid, int *relax_threads) {
+perrk_status perrk_tuning(const perrk_ctx *h, int *elems_per_cta, int *persistent_grid, int *relax_threads,
+                          int *stage_variant) {
     if (!h) return PERRK_INVALID_ARG;
     if (elems_per_cta) *elems_per_cta = h->c.stage_epb;
     if (persistent_grid) *persistent_grid = h->c.stage_persistent;
     if (relax_threads) *relax_threads = h->c.relax_threads;
+    if (stage_variant) *stage_variant = h->c.stage_variant;
+    return PERRK_OK;
+}
+
+perrk_status perrk_set_tuning(perrk_ctx *h, int elems_per_cta, int persistent_grid, int relax_threads,
+                              int stage_variant) {
+    if (!h) return PERRK_INVALID_ARG;
+    Ctx &c = h->c;
+    const bool epb_ok = c.dim == 1 ? (elems_per_cta == 16 || elems_per_cta == 32)
+                                   : (c.dim == 2 ? (elems_per_cta == 4 || elems_per_cta == 8 || elems_per_cta == 16)
+                                                 : (elems_per_cta == 1 || elems_per_cta == 2 || elems_per_cta == 4));
+    const bool box = c.opt.precision == PERRK_MIXED && c.equation != PERRK_BURGERS_1D && !c.curved && c.dim >= 2;
+    if (!epb_ok || persistent_grid < 0 || (relax_threads != 128 && relax_threads != 256) || stage_variant < 0 ||
+        stage_variant > 2 || (!box && stage_variant != 0 && stage_variant != c.stage_variant)) {
+        set_error("set_tuning: unsupported mapping for this context");
+        return PERRK_INVALID_ARG;
+    }
+    c.stage_epb = elems_per_cta;
+    c.stage_persistent = persistent_grid;
+    c.relax_threads = relax_threads;
+    c.stage_variant = box ? stage_variant : c.stage_variant;
+    c.graph_dirty = true;
     return PERRK_OK;
 }
 

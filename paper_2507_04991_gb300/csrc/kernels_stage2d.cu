@@ -2,7 +2,7 @@
 // so that the translation units compile in parallel).
 #include <cuda_runtime.h>
 
-#include "stage.cuh"
+#include "stage_box.cuh"
 
 namespace perrk {
 
@@ -37,6 +37,24 @@ cudaError_t stage_launch_2d(const StageParams &P, bool burgers, bool mixed, bool
     if (curved) { if (mixed) return go<EQ_EULER, float, true>(P, epb, grid, st); return go<EQ_EULER, double, true>(P, epb, grid, st); }
     if (mixed) return go<EQ_EULER, float, false>(P, epb, grid, st);
     return go<EQ_EULER, double, false>(P, epb, grid, st);
+}
+
+// mixed form on axis-aligned box elements; pipe: stage the next group's data with cp.async
+template <int EPB, bool PIPE>
+static cudaError_t box_go(const StageParams &P, int grid, cudaStream_t st) {
+    if constexpr (stage_box_smem_bytes<2, EPB, PIPE>() <= 48 * 1024) {
+        k_stage_box<2, EPB, PIPE><<<grid, EPB * ipow4(2), 0, st>>>(P);
+        return cudaGetLastError();
+    } else {
+        return cudaErrorInvalidConfiguration;
+    }
+}
+
+cudaError_t stage_launch_box_2d(const StageParams &P, int epb, bool pipe, int grid, cudaStream_t st) {
+    if (epb == 4) return pipe ? box_go<4, true>(P, grid, st) : box_go<4, false>(P, grid, st);
+    if (epb == 8) return pipe ? box_go<8, true>(P, grid, st) : box_go<8, false>(P, grid, st);
+    if (epb == 16) return pipe ? box_go<16, true>(P, grid, st) : box_go<16, false>(P, grid, st);
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace perrk

@@ -2,7 +2,7 @@
 // so that the translation units compile in parallel).
 #include <cuda_runtime.h>
 
-#include "stage.cuh"
+#include "stage_box.cuh"
 
 namespace perrk {
 
@@ -36,6 +36,24 @@ cudaError_t stage_launch_3d(const StageParams &P, bool burgers, bool mixed, bool
     (void)burgers; (void)curved;
     if (mixed) return go<EQ_EULER, float, false>(P, epb, grid, st);
     return go<EQ_EULER, double, false>(P, epb, grid, st);
+}
+
+// mixed form on axis-aligned box elements; pipe: stage the next group's data with cp.async
+template <int EPB, bool PIPE>
+static cudaError_t box_go(const StageParams &P, int grid, cudaStream_t st) {
+    if constexpr (stage_box_smem_bytes<3, EPB, PIPE>() <= 48 * 1024) {
+        k_stage_box<3, EPB, PIPE><<<grid, EPB * ipow4(3), 0, st>>>(P);
+        return cudaGetLastError();
+    } else {
+        return cudaErrorInvalidConfiguration;
+    }
+}
+
+cudaError_t stage_launch_box_3d(const StageParams &P, int epb, bool pipe, int grid, cudaStream_t st) {
+    if (epb == 1) return pipe ? box_go<1, true>(P, grid, st) : box_go<1, false>(P, grid, st);
+    if (epb == 2) return pipe ? box_go<2, true>(P, grid, st) : box_go<2, false>(P, grid, st);
+    if (epb == 4) return pipe ? box_go<4, true>(P, grid, st) : box_go<4, false>(P, grid, st);
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace perrk

@@ -34,14 +34,16 @@ struct StageCoef {
 
 // FP32 twin for the mixed form; b_i as a float pair (b_hi + b_lo) for the
 // double-float direction d += b_i K_i.
-struct StageCoefF {
+struct alignas(16) StageCoefF {
     float a1;
     float asub;
     float b_hi;
     float b_lo;
     int32_t has_b;    // b_i != 0
     int32_t first_b;  // first stage of the instance with b_i != 0
+    int32_t pad0, pad1;
 };
+static_assert(sizeof(StageCoefF) == 32, "StageCoefF is read as float4 + int2");
 
 // Per-instance relaxation scalars, resident in device memory.
 struct InstScalars {
@@ -99,6 +101,7 @@ struct Ctx {
     std::vector<int32_t> elist;               // elements sorted by E descending
     std::vector<int32_t> n_active;            // [S] active prefix length per stage
     std::vector<int32_t> any_b;               // [S] 1 if some instance has b_i != 0
+    std::vector<int32_t> d_read;              // [S] 1 if some instance adds to an existing d at this stage
     std::vector<int32_t> chunk_inst, chunk_e0, chunk_e1;
     int chunk_elems = 0;
     // host geometry (double)
@@ -142,6 +145,7 @@ struct Ctx {
     int stage_epb = 0;                        // elements per CTA in the stage kernel
     int stage_persistent = 0;                 // grid = min(groups, persistent blocks)
     int relax_threads = 128;
+    int stage_variant = 1;                    // mixed box: 0 generic kernel, 1 box kernel, 2 box kernel + cp.async staging
     bool tuned = false;
 
     // CUDA graph of one step

@@ -308,6 +308,15 @@ perrk_status build_ctx(Ctx &c, int n, const perrk_mesh_desc *mesh, const perrk_s
             c.nbr[gR * NF + fR] = (int32_t)gL;
         }
     }
+    // every face of every element needs a partner (interior or periodic): the
+    // method has no boundary conditions here, and the kernels index nbr[] directly
+    for (size_t i = 0; i < c.nbr.size(); ++i)
+        if (c.nbr[i] < 0) {
+            snprintf(buf, sizeof buf, "element %zu face %zu has no partner face (boundary faces are not supported)",
+                     i / (size_t)NF, i % (size_t)NF);
+            err = buf;
+            return PERRK_INVALID_ARG;
+        }
     // canonical face normals: the '+' side's Ja^k at its face nodes, shared by both sides
     if (c.curved) {
         c.fnorm.assign(NE * NF * NFP * 2, 0.0);
@@ -368,10 +377,16 @@ perrk_status build_ctx(Ctx &c, int n, const perrk_mesh_desc *mesh, const perrk_s
         c.n_active[i - 1] = cnt;
     }
     c.any_b.assign(S, 0);
+    c.d_read.assign(S, 0);
     for (int k = 0; k < n; ++k) {
         const Instance &I = c.inst[k];
+        bool seen_b = false;
         for (int j = 0; j < I.S; ++j)
-            if (I.b[j] != 0.0) c.any_b[j == 0 ? 0 : S - I.S + j] = 1;
+            if (I.b[j] != 0.0) {
+                c.any_b[j == 0 ? 0 : S - I.S + j] = 1;
+                if (seen_b) c.d_read[j == 0 ? 0 : S - I.S + j] = 1;
+                seen_b = true;
+            }
     }
     make_chunks(c, 152);
     return PERRK_OK;
@@ -403,7 +418,7 @@ void make_chunks(Ctx &c, int sm_count) {
 
 void stage_coefficients(const Ctx &c, std::vector<StageCoef> &coef, std::vector<StageCoefF> &coef_f) {
     coef.assign((size_t)c.S * c.n_gp, StageCoef{0, 0, 0, 0});
-    coef_f.assign((size_t)c.S * c.n_gp, StageCoefF{0, 0, 0, 0, 0, 0});
+    coef_f.assign((size_t)c.S * c.n_gp, StageCoefF{0, 0, 0, 0, 0, 0, 0, 0});
     for (const Instance &I : c.inst) {
         int first_b = -1;
         for (int j = 0; j < I.S; ++j)
@@ -424,7 +439,7 @@ void stage_coefficients(const Ctx &c, std::vector<StageCoef> &coef, std::vector<
                 const float b_hi = (float)sc.b;
                 const float b_lo = (float)(sc.b - (double)b_hi);
                 coef_f[(size_t)i * c.n_gp + I.gp0 + r] =
-                    StageCoefF{(float)sc.a1, (float)sc.asub, b_hi, b_lo, sc.b != 0.0 ? 1 : 0, j == first_b ? 1 : 0};
+                    StageCoefF{(float)sc.a1, (float)sc.asub, b_hi, b_lo, sc.b != 0.0 ? 1 : 0, j == first_b ? 1 : 0, 0, 0};
             }
         }
     }

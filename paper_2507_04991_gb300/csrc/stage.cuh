@@ -36,6 +36,7 @@ struct StageParams {
     int n_active;
     int stage1;                 // U_{n,1} = U_n: no K loads
     int do_b;                   // some element has b_i != 0 at this stage
+    int d_read;                 // some element adds to an existing direction d at this stage
     int es;                     // Rusanov dissipation on the surface flux
     const float *g_node_f, *g_elem_f, *fnorm_f, *wJ_f;   // FP32 geometry (mixed form)
     double gamma_gas;

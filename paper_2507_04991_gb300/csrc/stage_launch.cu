@@ -11,6 +11,8 @@ namespace perrk {
 cudaError_t stage_launch_1d(const StageParams &, bool, bool, bool, int, int, cudaStream_t);
 cudaError_t stage_launch_2d(const StageParams &, bool, bool, bool, int, int, cudaStream_t);
 cudaError_t stage_launch_3d(const StageParams &, bool, bool, bool, int, int, cudaStream_t);
+cudaError_t stage_launch_box_2d(const StageParams &, int, bool, int, cudaStream_t);
+cudaError_t stage_launch_box_3d(const StageParams &, int, bool, int, cudaStream_t);
 
 int default_epb(int dim) { return dim == 1 ? 32 : (dim == 2 ? 8 : 2); }
 
@@ -89,6 +91,7 @@ perrk_status launch_stage(Ctx &c, int stage, bool rhs_only, const double *in_u, 
     P.n_active = rhs_only ? c.n_elem : c.n_active[stage];
     P.stage1 = (stage == 0 || rhs_only) ? 1 : 0;
     P.do_b = (!rhs_only && c.any_b[stage]) ? 1 : 0;
+    P.d_read = (!rhs_only && c.d_read[stage]) ? 1 : 0;
     P.es = c.surface == PERRK_SURFACE_ES_RUSANOV ? 1 : 0;
     P.gamma_gas = c.gamma_gas;
     for (int i = 0; i < 16; ++i) {
@@ -115,13 +118,18 @@ perrk_status launch_stage(Ctx &c, int stage, bool rhs_only, const double *in_u, 
         set_error("geometry tables missing for the selected geometry mode");
         return PERRK_INVALID_ARG;
     }
+    const bool burgers = c.equation == PERRK_BURGERS_1D;
+    // mixed form on box elements: kernel variant 0 = the generic stage kernel,
+    // 1 = the float4 box kernel, 2 = the box kernel with cp.async staging
+    const bool box = mixed && !burgers && !c.curved && c.dim >= 2 && c.stage_variant > 0;
     const int epb = c.stage_epb > 0 ? c.stage_epb : default_epb(c.dim);
     const int groups = (P.n_active + epb - 1) / epb;
     int grid = groups;
     if (c.stage_persistent > 0) grid = std::min(groups, c.stage_persistent);
-    const bool burgers = c.equation == PERRK_BURGERS_1D;
     cudaError_t e;
-    if (c.dim == 1) e = stage_launch_1d(P, burgers, mixed, c.curved, epb, grid, (cudaStream_t)stream);
+    if (box && c.dim == 2) e = stage_launch_box_2d(P, epb, c.stage_variant == 2, grid, (cudaStream_t)stream);
+    else if (box && c.dim == 3) e = stage_launch_box_3d(P, epb, c.stage_variant == 2, grid, (cudaStream_t)stream);
+    else if (c.dim == 1) e = stage_launch_1d(P, burgers, mixed, c.curved, epb, grid, (cudaStream_t)stream);
     else if (c.dim == 2) e = stage_launch_2d(P, burgers, mixed, c.curved, epb, grid, (cudaStream_t)stream);
     else e = stage_launch_3d(P, burgers, mixed, c.curved, epb, grid, (cudaStream_t)stream);
     return cuda_check((int)e, "stage launch");

@@ -53,7 +53,8 @@ def _small_mesh():
     return wl, keep, m, tab
 
 
-@pytest.mark.parametrize("breakage", ["bad_rowsum", "bad_E", "bad_part", "bad_face", "bad_b", "bad_N", "asub_inactive"])
+@pytest.mark.parametrize("breakage", ["bad_rowsum", "bad_E", "bad_part", "bad_face", "missing_face", "bad_b", "bad_N",
+                                      "asub_inactive"])
 def test_invalid_input_rejected(lib, breakage):
     wl, keep, m, (c, b, a1, asub) = _small_mesh()
     c, b, a1, asub = c.copy(), b.copy(), a1.copy(), asub.copy()
@@ -68,6 +69,8 @@ def test_invalid_input_rejected(lib, breakage):
         part[0] = 5
     elif breakage == "bad_face":
         faces[0, 3] = 2
+    elif breakage == "missing_face":
+        faces = faces[1:]          # one element face pair left without partner
     elif breakage == "bad_b":
         b[1] = 0.1
     elif breakage == "asub_inactive":

@@ -60,5 +60,40 @@ def test_autotune_keeps_results_bitwise(precision):
     u2 = s2.state()
     s2.close()
     assert tuning["elems_per_cta"] in (4, 8, 16) and tuning["relax_threads"] in (128, 256)
+    assert tuning["stage_variant"] in (0, 1, 2)
     assert np.array_equal(u1, u2)
     assert [a[0]["gamma"] for a in r1] == [a[0]["gamma"] for a in r2]
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_mixed_stage_kernel_variants_bitwise(dim):
+    """The mixed form's three stage kernels (generic, float4 box kernel, box
+    kernel with cp.async staging) under every elements-per-CTA and grid
+    choice give bit-identical steps (same arithmetic in the same order)."""
+    if dim == 2:
+        wl = workloads.small_box_2d(n=12, seed=47, R=2, E=[6, 3], order=3, ic="khi")
+        epbs = (4, 8, 16)
+    else:
+        wl = workloads.tgv_3d(n=8, n_fine=4)
+        epbs = (1, 2, 4)
+    ref = None
+    for variant in (0, 1, 2):
+        for epb in epbs:
+            for grid in (0, 152):
+                s = pk.Solver(wl, pk.options(precision=pk.MIXED, use_graph=True))
+                try:
+                    pk.perrk_set_tuning(s.h, epb, grid, 128, variant)
+                    s.set_state(wl.u0)
+                    recs = s.step(3)
+                except pk.PerrkError as err:
+                    # a mapping whose shared memory does not fit is refused at launch
+                    assert "invalid configuration" in str(err) or "configuration" in pk.last_error()
+                    s.close()
+                    continue
+                out = (s.state(), [r[0]["gamma"] for r in recs])
+                s.close()
+                if ref is None:
+                    ref = out
+                assert np.array_equal(out[0], ref[0]), (variant, epb, grid)
+                assert out[1] == ref[1], (variant, epb, grid)
+    assert ref is not None
