@@ -141,6 +141,26 @@ def reduce_over_ranks(x, world, op):
     return float(t.item())
 
 
+# DRAM traffic of the roofline kernel (all-active stage of the batched 2D
+# workload, generic mixed stage kernel) from one ncu capture of the full-size
+# launch (profiles/k_stage_batched2d_traffic.md).  It is reported only while
+# the stage kernel sources are the ones that capture measured.
+STAGE_TRAFFIC = {"workload": "batched2d", "stage_variant": 0, "bytes": 2431864064 + 1228096000,
+                 "sources_sha256": "4d75f7c498b7f591ff8b1ac6b7c697afa9394fc845d30525bdee5c13cf58c7cc"}
+STAGE_SOURCES = ["stage.cuh", "stage_box.cuh", "physics.cuh", "dfloat.cuh", "kernels_stage2d.cu", "stage_launch.cu"]
+
+
+def stage_traffic(workload, variant):
+    import hashlib
+    h = hashlib.sha256()
+    for f in STAGE_SOURCES:
+        with open(os.path.join(ROOT, "paper_2507_04991_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    ok = (workload == STAGE_TRAFFIC["workload"] and variant == STAGE_TRAFFIC["stage_variant"]
+          and h.hexdigest() == STAGE_TRAFFIC["sources_sha256"])
+    return STAGE_TRAFFIC["bytes"] if ok else None
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -235,7 +255,11 @@ def run_native(args):
     # double-float entropy noise, so the mixed form stops at 1e-12 A.
     mixed_opts = dict(precision=pk.MIXED, use_graph=True, max_it=args.max_it, tol_r=args.mixed_tol_r)
     chosen = pk.Solver(insts, pk.options(guess=pk.GUESS_MLP, **mixed_opts))
-    pk.perrk_autotune(chosen.h, stream=sh)
+    if args.tuning:
+        epb, grid, var = (int(x) for x in args.tuning.split(","))
+        pk.perrk_set_tuning(chosen.h, epb, grid, 128, var)
+    else:
+        pk.perrk_autotune(chosen.h, stream=sh)
     chosen.set_state(u0)
     chosen.set_mlp(W)
     tuning = pk.perrk_tuning(chosen.h)
@@ -374,7 +398,7 @@ def run_native(args):
                           "newton_guess_comparison_steps_4_to_10": guesses,
                           "newton_tol_r": {"mixed": args.mixed_tol_r, "fp64": 1e-14}},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "kernel": f"k_stage (stage {S}, {st['n_active']} elements, all active)",
+                     "traffic": stage_traffic(args.workload, tuning["stage_variant"]), "kernel": f"k_stage (stage {S}, {st['n_active']} elements, all active)",
                      "algorithmic_bytes": st["bytes"], "kernel_ms": 1e3 * k_s, "peak_source": peak_src},
         "cpu_baseline": {"value": cpu[0], "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"one oracle step each of the first {cpu[1]} instances ({cpu[2]:.1f} s, numpy float64, one thread)"},
@@ -396,6 +420,9 @@ def main():
     ap.add_argument("--train-steps", type=int, default=30)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--mixed-tol-r", type=float, default=1e-12)
+    ap.add_argument("--tuning", default=None,
+                    help="EPB,GRID,VARIANT: pin the chosen form's stage mapping instead of autotuning it "
+                         "(reproducible profiling)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
