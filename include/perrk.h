@@ -104,6 +104,10 @@ typedef struct {
     int guess;                    /* perrk_guess: initial Newton guess */
     int target;                   /* perrk_target: which entropy equality is enforced */
     int use_graph;                /* 1: capture one step in a CUDA graph and replay it */
+    int fuse_direction;           /* 1 (default): when every b_i != 0 sits at a first, penultimate or last
+                                     stage (all archetypes), form d = sum b_i K_i once at the last stage
+                                     from K_1, K_{S-1}, K_S; 0: accumulate d at every stage with b_i != 0.
+                                     Same sums in the same order either way. */
 } perrk_options;
 
 /* Per-step record (perrk_step fills one per step when info != NULL). */
@@ -123,7 +127,8 @@ typedef struct {
 typedef struct perrk_ctx perrk_ctx;
 
 /* Fill opts with defaults: FP64, relaxed, max_it 10, tol_r 1e-14, tol_g 1e-14,
- * guess PREV (Sec. 3.1: gamma_{n-1}, 1 at the first step), target DELTA_H, no graph. */
+ * guess PREV (Sec. 3.1: gamma_{n-1}, 1 at the first step), target DELTA_H, no
+ * graph, fused direction. */
 void perrk_default_options(perrk_options *opts);
 
 /* Validate and copy mesh and scheme, compute LGL tables and metric terms,

@@ -50,7 +50,7 @@ class perrk_scheme_desc(C.Structure):
 class perrk_options(C.Structure):
     _fields_ = [("precision", C.c_int), ("relaxation", C.c_int), ("newton_max_it", C.c_int),
                 ("newton_tol_r", C.c_double), ("newton_tol_g", C.c_double), ("guess", C.c_int),
-                ("target", C.c_int), ("use_graph", C.c_int)]
+                ("target", C.c_int), ("use_graph", C.c_int), ("fuse_direction", C.c_int)]
 
 
 class perrk_step_info(C.Structure):
@@ -414,7 +414,7 @@ SURFACE_CODES = {"ec": SURFACE_EC, "es": SURFACE_ES_RUSANOV, "es_rusanov": SURFA
 
 
 def options(precision=FP64, relaxation=True, max_it=10, tol_r=1e-14, tol_g=1e-14, guess=GUESS_PREV,
-            target=TARGET_DELTA_H, use_graph=False):
+            target=TARGET_DELTA_H, use_graph=False, fuse_direction=True):
     o = perrk_default_options()
     o.precision = precision
     o.relaxation = int(bool(relaxation))
@@ -424,6 +424,7 @@ def options(precision=FP64, relaxation=True, max_it=10, tol_r=1e-14, tol_g=1e-14
     o.guess = guess
     o.target = target
     o.use_graph = int(bool(use_graph))
+    o.fuse_direction = int(bool(fuse_direction))
     return o
 
 

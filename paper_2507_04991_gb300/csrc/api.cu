@@ -185,6 +185,7 @@ void perrk_default_options(perrk_options *o) {
     o->guess = PERRK_GUESS_PREV;
     o->target = PERRK_TARGET_DELTA_H;
     o->use_graph = 0;
+    o->fuse_direction = 1;
 }
 
 perrk_status perrk_create_batched(int n, const perrk_mesh_desc *mesh, const perrk_scheme_desc *scheme,
@@ -490,7 +491,8 @@ perrk_status perrk_stage_info(const perrk_ctx *h, int stage, int64_t *n_active, 
         if (stage > 0) arrays += 1;               // K_1
         if (stage > 0 && sc.asub != 0.0) arrays += 1;  // K_{i-1}
         int64_t dbytes = 0;
-        if (sc.b != 0.0) dbytes = ((sc.first_b != 0.0) ? 1 : 2) * per_d;  // d write (and read)
+        if (c.d_fused) dbytes = sc.d_final != 0.0 ? per_d : 0;             // d written once, at the last stage
+        else if (sc.b != 0.0) dbytes = ((sc.first_b != 0.0) ? 1 : 2) * per_d;  // d write (and read)
         int64_t geo = c.curved ? (int64_t)c.NP * 5 * 8 + (int64_t)NF * NFP * 2 * 8 : (int64_t)(c.dim + 1 + NF) * 8;
         if (sc.b != 0.0) geo += (int64_t)c.NP * 8 + 8;  // omega J and the element's Delta H slot
         tot += arrays * per_arr + dbytes + geo + 4 * (2 + NF);  // element list, partition id, neighbours

@@ -30,6 +30,10 @@ struct StageCoef {
     double asub;
     double b;        // b_i of the instance (the direction d += b K_i)
     double first_b;  // 1.0 at the instance's first stage with b != 0
+    // fused direction (all b_i != 0 at the first, penultimate and last stage):
+    // at the last stage d = b_1 K_1 + b_m K_{S-1} + b_S K_S in one write
+    double b1, bm;   // b of the first and of the penultimate stage (bm = 0 if S = 2)
+    double d_final;  // 1.0 at the last stage when the direction is fused
 };
 
 // FP32 twin for the mixed form; b_i as a float pair (b_hi + b_lo) for the
@@ -41,9 +45,11 @@ struct alignas(16) StageCoefF {
     float b_lo;
     int32_t has_b;    // b_i != 0
     int32_t first_b;  // first stage of the instance with b_i != 0
-    int32_t pad0, pad1;
+    int32_t d_final;  // last stage of a fused direction (see StageCoef)
+    int32_t pad0;
+    float b1_hi, b1_lo, bm_hi, bm_lo;   // b_1 and b_m as float pairs
 };
-static_assert(sizeof(StageCoefF) == 32, "StageCoefF is read as float4 + int2");
+static_assert(sizeof(StageCoefF) == 48, "StageCoefF is read as float4 + int4 + float4");
 
 // Per-instance relaxation scalars, resident in device memory.
 struct InstScalars {
@@ -102,6 +108,7 @@ struct Ctx {
     std::vector<int32_t> n_active;            // [S] active prefix length per stage
     std::vector<int32_t> any_b;               // [S] 1 if some instance has b_i != 0
     std::vector<int32_t> d_read;              // [S] 1 if some instance adds to an existing d at this stage
+    bool d_fused = false;                     // every instance: b_i != 0 only at its first, penultimate, last stage
     std::vector<int32_t> chunk_inst, chunk_e0, chunk_e1;
     int chunk_elems = 0;
     // host geometry (double)

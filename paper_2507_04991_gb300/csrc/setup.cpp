@@ -376,6 +376,16 @@ perrk_status build_ctx(Ctx &c, int n, const perrk_mesh_desc *mesh, const perrk_s
         }
         c.n_active[i - 1] = cnt;
     }
+    // fused direction: with b_i != 0 only at the first, penultimate and last
+    // stage (all archetypes), d = b_1 K_1 + b_m K_{S-1} + b_S K_S is formed at
+    // the last stage, where K_1 and K_{S-1} are read for the stage row anyway
+    c.d_fused = c.opt.fuse_direction != 0;
+    for (int k = 0; k < n; ++k) {
+        const Instance &I = c.inst[k];
+        for (int j = 1; j < I.S - 2; ++j)
+            if (I.b[j] != 0.0) c.d_fused = false;
+        if (I.S < 2) c.d_fused = false;
+    }
     c.any_b.assign(S, 0);
     c.d_read.assign(S, 0);
     for (int k = 0; k < n; ++k) {
@@ -384,7 +394,7 @@ perrk_status build_ctx(Ctx &c, int n, const perrk_mesh_desc *mesh, const perrk_s
         for (int j = 0; j < I.S; ++j)
             if (I.b[j] != 0.0) {
                 c.any_b[j == 0 ? 0 : S - I.S + j] = 1;
-                if (seen_b) c.d_read[j == 0 ? 0 : S - I.S + j] = 1;
+                if (seen_b && !c.d_fused) c.d_read[j == 0 ? 0 : S - I.S + j] = 1;
                 seen_b = true;
             }
     }
@@ -417,8 +427,12 @@ void make_chunks(Ctx &c, int sm_count) {
 }
 
 void stage_coefficients(const Ctx &c, std::vector<StageCoef> &coef, std::vector<StageCoefF> &coef_f) {
-    coef.assign((size_t)c.S * c.n_gp, StageCoef{0, 0, 0, 0});
-    coef_f.assign((size_t)c.S * c.n_gp, StageCoefF{0, 0, 0, 0, 0, 0, 0, 0});
+    coef.assign((size_t)c.S * c.n_gp, StageCoef{0, 0, 0, 0, 0, 0, 0});
+    coef_f.assign((size_t)c.S * c.n_gp, StageCoefF{0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0});
+    auto split = [](double v, float &hi, float &lo) {
+        hi = (float)v;
+        lo = (float)(v - (double)hi);
+    };
     for (const Instance &I : c.inst) {
         int first_b = -1;
         for (int j = 0; j < I.S; ++j)
@@ -436,10 +450,19 @@ void stage_coefficients(const Ctx &c, std::vector<StageCoef> &coef, std::vector<
                 sc.asub = I.dt * I.asub[r * I.S + j];
                 sc.b = I.b[j];
                 sc.first_b = (j == first_b) ? 1.0 : 0.0;
-                const float b_hi = (float)sc.b;
-                const float b_lo = (float)(sc.b - (double)b_hi);
-                coef_f[(size_t)i * c.n_gp + I.gp0 + r] =
-                    StageCoefF{(float)sc.a1, (float)sc.asub, b_hi, b_lo, sc.b != 0.0 ? 1 : 0, j == first_b ? 1 : 0, 0, 0};
+                const bool last = c.d_fused && j == I.S - 1;
+                sc.b1 = last ? I.b[0] : 0.0;
+                sc.bm = (last && I.S - 2 > 0) ? I.b[I.S - 2] : 0.0;
+                sc.d_final = last ? 1.0 : 0.0;
+                StageCoefF &cf = coef_f[(size_t)i * c.n_gp + I.gp0 + r];
+                cf.a1 = (float)sc.a1;
+                cf.asub = (float)sc.asub;
+                split(sc.b, cf.b_hi, cf.b_lo);
+                cf.has_b = sc.b != 0.0 ? 1 : 0;
+                cf.first_b = j == first_b ? 1 : 0;
+                cf.d_final = last ? 1 : 0;
+                split(sc.b1, cf.b1_hi, cf.b1_lo);
+                split(sc.bm, cf.bm_hi, cf.bm_lo);
             }
         }
     }

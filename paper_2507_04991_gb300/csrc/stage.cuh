@@ -37,6 +37,7 @@ struct StageParams {
     int stage1;                 // U_{n,1} = U_n: no K loads
     int do_b;                   // some element has b_i != 0 at this stage
     int d_read;                 // some element adds to an existing direction d at this stage
+    int d_fused;                // d = b_1 K_1 + b_m K_{S-1} + b_S K_S written once at the last stage
     int es;                     // Rusanov dissipation on the surface flux
     const float *g_node_f, *g_elem_f, *fnorm_f, *wJ_f;   // FP32 geometry (mixed form)
     double gamma_gas;
@@ -108,7 +109,7 @@ __device__ __forceinline__ void stage_state(const StageParams &P, size_t NPtot, 
         for (int v = 0; v < V; ++v) {
             Ud[v] = __ldg(P.U + v * NPtot + idx);
             K1d[v] = __ldg(P.K1 + v * NPtot + idx);
-            Kpd[v] = (c.asub != 0.0) ? __ldg(P.Kprev + v * NPtot + idx) : 0.0;
+            Kpd[v] = (c.asub != 0.0 || c.bm != 0.0) ? __ldg(P.Kprev + v * NPtot + idx) : 0.0;
         }
 #pragma unroll
         for (int v = 0; v < V; ++v) u[v] = (Real)fma(c.asub, Kpd[v], fma(c.a1, K1d[v], Ud[v]));
@@ -139,8 +140,15 @@ constexpr size_t stage_smem_bytes() {
            sizeof(double) * (size_t)EPB * NP;
 }
 
+// Occupancy of the 2D mixed-form kernel: <= 40 registers per thread (12 CTAs
+// of 128 threads per SM hide the global-load latency); other forms unbounded.
+template <int DIM, typename Real, int EPB>
+constexpr int stage_min_blocks() {
+    return (DIM == 2 && sizeof(Real) == 4 && EPB >= 8) ? 1536 / (EPB * ipow4(DIM)) : 1;
+}
+
 template <int DIM, int EQ, typename Real, bool CURVED, int EPB>
-__global__ void __launch_bounds__(EPB * ipow4(DIM)) k_stage(const StageParams P) {
+__global__ void __launch_bounds__(EPB * ipow4(DIM), stage_min_blocks<DIM, Real, EPB>()) k_stage(const StageParams P) {
     constexpr int NP = ipow4(DIM), NF = 2 * DIM, NFP = ipow4(DIM - 1);
     constexpr int V = EQ == EQ_BURGERS ? 1 : DIM + 2;
     constexpr int NPR = EQ == EQ_BURGERS ? 1 : DIM + 5;
@@ -152,6 +160,7 @@ __global__ void __launch_bounds__(EPB * ipow4(DIM)) k_stage(const StageParams P)
     constexpr int NLINE = DIM * ipow4(DIM - 1);       // reference lines per element
     constexpr int NPAIR = NLINE * 6;                  // node pairs (q < m) on those lines
     __shared__ Real s_pf[EPB][NPAIR][V];              // two-point volume fluxes, one per pair
+
 
     constexpr bool MIX = sizeof(Real) == 4;           // mixed form: no float64 instruction per node
     const int el = threadIdx.x / NP, q = threadIdx.x % NP;
@@ -196,6 +205,7 @@ __global__ void __launch_bounds__(EPB * ipow4(DIM)) k_stage(const StageParams P)
         Real u[V];
         double Ud[V], K1d[V], Kpd[V];
         stage_state<V, Real>(P, NPtot, idx, g, u, Ud, K1d, Kpd);
+
 #pragma unroll
         for (int v = 0; v < V; ++v) s_u[el][v][q] = u[v];
         if constexpr (EQ == EQ_EULER) {
@@ -490,12 +500,20 @@ __global__ void __launch_bounds__(EPB * ipow4(DIM)) k_stage(const StageParams P)
                         wdf = dfma(w0, k0, gm1 * rho * ip * (mk - kE));
                     }
                     wdf *= __ldg(P.wJ_f + idx);
-                    if (valid) {
+                    if (valid && (!P.d_fused || cf.d_final)) {
                         const df bb{cf.b_hi, cf.b_lo};
 #pragma unroll
                         for (int v = 0; v < V; ++v) {
                             const size_t j = v * NPtot + idx;
-                            const df dn = cf.first_b ? df_mul_f(bb, Kr[v]) : df_fma_f(df{P.dh[j], P.dl[j]}, bb, Kr[v]);
+                            df dn;
+                            if (P.d_fused) {
+                                // d = b_1 K_1 + b_m K_{S-1} + b_S K_S (the sums of the stage-by-stage form)
+                                dn = df_mul_f(df{cf.b1_hi, cf.b1_lo}, __ldg(P.K1f + j));   // L2-resident: read by the stage row
+                                dn = df_fma_f(dn, df{cf.bm_hi, cf.bm_lo}, __ldg(P.Kprevf + j));
+                                dn = df_fma_f(dn, bb, Kr[v]);
+                            } else {
+                                dn = cf.first_b ? df_mul_f(bb, Kr[v]) : df_fma_f(df{P.dh[j], P.dl[j]}, bb, Kr[v]);
+                            }
                             P.dh[j] = dn.hi;
                             P.dl[j] = dn.lo;
                         }
@@ -536,7 +554,15 @@ __global__ void __launch_bounds__(EPB * ipow4(DIM)) k_stage(const StageParams P)
                     for (int v = 0; v < V; ++v) wdot = fma(w[v], (double)Kr[v], wdot);
                 }
                 wdot *= __ldg(P.wJ + idx);
-                if (valid) {
+                if (valid && P.d_fused) {
+                    // d = b_1 K_1 + b_m K_{S-1} + b_S K_S at the last stage (the
+                    // stage-by-stage sums in the same order)
+                    if (c.d_final != 0.0) {
+#pragma unroll
+                        for (int v = 0; v < V; ++v)
+                            P.d[v * NPtot + idx] = fma(c.b, (double)Kr[v], fma(c.bm, Kpd[v], c.b1 * K1d[v]));
+                    }
+                } else if (valid) {
 #pragma unroll
                     for (int v = 0; v < V; ++v) {
                         double dold = (c.first_b != 0.0) ? 0.0 : P.d[v * NPtot + idx];

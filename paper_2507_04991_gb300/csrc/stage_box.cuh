@@ -460,12 +460,12 @@ __global__ void __launch_bounds__(EPB * ipow4(DIM), box_min_blocks<DIM, EPB, PIP
         // d += b_i K_i and the element's running sum as float pairs
         if (P.do_b) {
             const float4 cb = __ldg(reinterpret_cast<const float4 *>(P.coef_f + g));        // a1, asub, b_hi, b_lo
-            const int2 fl = __ldg(reinterpret_cast<const int2 *>(&P.coef_f[g].has_b));     // has_b, first_b
+            const int4 fl = __ldg(reinterpret_cast<const int4 *>(&P.coef_f[g].has_b));     // has_b, first_b, d_final
             float wdf = 0.0f;
             if (fl.x) {
                 if constexpr (!PIPE) {
                     wj = __ldg(P.wJ_f + idx);
-                    if (!fl.y) {
+                    if (!fl.y && !P.d_fused) {
 #pragma unroll
                         for (int v = 0; v < V; ++v) {
                             dprev[v] = P.dh[v * NPtot + idx];
@@ -483,12 +483,21 @@ __global__ void __launch_bounds__(EPB * ipow4(DIM), box_min_blocks<DIM, EPB, PIP
                 }
                 const float w0 = gam - Sl - gm1 * 0.5f * pr.rho * v2 * ip;
                 wdf = fmaf(w0, Kr[0], gm1 * pr.rho * ip * (mk - Kr[DIM + 1])) * wj;
-                if (valid) {
+                if (valid && (!P.d_fused || fl.z)) {
                     const df bb{cb.z, cb.w};
+                    const float4 cbm = __ldg(reinterpret_cast<const float4 *>(&P.coef_f[g].b1_hi));   // b1, bm pairs
 #pragma unroll
                     for (int v = 0; v < V; ++v) {
                         const size_t j = v * NPtot + idx;
-                        const df dn = fl.y ? df_mul_f(bb, Kr[v]) : df_fma_f(df{dprev[v], dprev[V + v]}, bb, Kr[v]);
+                        df dn;
+                        if (P.d_fused) {
+                            // d = b_1 K_1 + b_m K_{S-1} + b_S K_S (the sums of the stage-by-stage form)
+                            dn = df_mul_f(df{cbm.x, cbm.y}, __ldg(P.K1f + j));   // L2-resident: read by the stage row
+                            dn = df_fma_f(dn, df{cbm.z, cbm.w}, __ldg(P.Kprevf + j));
+                            dn = df_fma_f(dn, bb, Kr[v]);
+                        } else {
+                            dn = fl.y ? df_mul_f(bb, Kr[v]) : df_fma_f(df{dprev[v], dprev[V + v]}, bb, Kr[v]);
+                        }
                         P.dh[j] = dn.hi;
                         P.dl[j] = dn.lo;
                     }

@@ -92,6 +92,7 @@ perrk_status launch_stage(Ctx &c, int stage, bool rhs_only, const double *in_u, 
     P.stage1 = (stage == 0 || rhs_only) ? 1 : 0;
     P.do_b = (!rhs_only && c.any_b[stage]) ? 1 : 0;
     P.d_read = (!rhs_only && c.d_read[stage]) ? 1 : 0;
+    P.d_fused = c.d_fused ? 1 : 0;
     P.es = c.surface == PERRK_SURFACE_ES_RUSANOV ? 1 : 0;
     P.gamma_gas = c.gamma_gas;
     for (int i = 0; i < 16; ++i) {

@@ -97,3 +97,20 @@ def test_mixed_stage_kernel_variants_bitwise(dim):
                 assert np.array_equal(out[0], ref[0]), (variant, epb, grid)
                 assert out[1] == ref[1], (variant, epb, grid)
     assert ref is not None
+
+
+@pytest.mark.parametrize("precision", [pk.FP64, pk.MIXED])
+def test_fused_direction_bitwise(precision):
+    """d formed once at the last stage from K_1, K_{S-1}, K_S equals d
+    accumulated stage by stage, bit for bit (same sums in the same order), for
+    p = 2, 3 and 4 families."""
+    for order, E in ((2, [6, 3]), (3, [6, 3]), (4, [8, 5])):
+        wl = workloads.small_box_2d(n=8, seed=53, R=2, E=E, order=order, ic="khi")
+        outs = []
+        for fuse in (True, False):
+            s = pk.Solver(wl, pk.options(precision=precision, fuse_direction=fuse))
+            recs = s.step(3)
+            outs.append((s.state(), [r[0]["gamma"] for r in recs], [r[0]["dH"] for r in recs]))
+            s.close()
+        assert np.array_equal(outs[0][0], outs[1][0]), order
+        assert outs[0][1] == outs[1][1] and outs[0][2] == outs[1][2], order
