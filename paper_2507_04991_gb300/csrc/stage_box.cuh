@@ -42,21 +42,57 @@ struct BoxShape {
 
 // primitives <-> two float4: 2D (rho, v0, v1, p) (beta, lrho, lbeta, -);
 // 3D (rho, v0, v1, v2) (p, beta, lrho, lbeta)
+// Shared-memory slots.  A warp's 16-byte loads are served eight threads at a
+// time, without conflict when the eight addresses fall in distinct 16-byte
+// bank groups (address / 16 mod 8) or coincide.  2D: the node and pair-flux
+// slots below are permutations found by exhaustive local search over the
+// kernel's access pattern (each quarter warp is a row pair of one element):
+// every float4 access of the primitives, states and pair fluxes is then
+// conflict-free.  3D: an XOR swizzle for the nodes, pair fluxes in order.
+constexpr unsigned long long kNodeSlot2 = 0x71a86c5320f9dbe4ull;   // 4 bits per node
+// pair slots: 8 bits per pair, eight pairs per word
+constexpr unsigned long long kPairSlot2_0 = 0x0c221b2916002d07ull;
+constexpr unsigned long long kPairSlot2_1 = 0x120b2521042f1026ull;
+constexpr unsigned long long kPairSlot2_2 = 0x27242b2e202a0d19ull;
+constexpr unsigned long long kPairSlot2_3 = 0x281c0215011e230full;
+constexpr unsigned long long kPairSlot2_4 = 0x0e091d1803141f1aull;
+constexpr unsigned long long kPairSlot2_5 = 0x06080a172c110513ull;   // 8 bits per pair
+
 template <int DIM>
-__device__ __forceinline__ void prim_store(float4 *s, const Prim<float, DIM> &P) {
+__device__ __forceinline__ int node_slot(int n) {
+    if constexpr (DIM == 2) return (int)((kNodeSlot2 >> (4 * n)) & 15u);
+    else return n ^ ((n >> 3) & 7);
+}
+template <int DIM>
+__device__ __forceinline__ int pair_slot(int pp) {
     if constexpr (DIM == 2) {
-        s[0] = make_float4(P.rho, P.v[0], P.v[1], P.p);
-        s[1] = make_float4(P.beta, P.lrho, P.lbeta, 0.0f);
+        const int w = pp >> 3;
+        unsigned long long x = kPairSlot2_0;
+        x = (w == 1) ? kPairSlot2_1 : x;
+        x = (w == 2) ? kPairSlot2_2 : x;
+        x = (w == 3) ? kPairSlot2_3 : x;
+        x = (w == 4) ? kPairSlot2_4 : x;
+        x = (w == 5) ? kPairSlot2_5 : x;
+        return (int)((x >> (8 * (pp & 7))) & 255u);
+    }
+    else return pp;
+}
+
+template <int DIM>
+__device__ __forceinline__ void prim_store(float4 *pa, float4 *pb, const Prim<float, DIM> &P) {
+    if constexpr (DIM == 2) {
+        *pa = make_float4(P.rho, P.v[0], P.v[1], P.p);
+        *pb = make_float4(P.beta, P.lrho, P.lbeta, 0.0f);
     } else {
-        s[0] = make_float4(P.rho, P.v[0], P.v[1], P.v[2]);
-        s[1] = make_float4(P.p, P.beta, P.lrho, P.lbeta);
+        *pa = make_float4(P.rho, P.v[0], P.v[1], P.v[2]);
+        *pb = make_float4(P.p, P.beta, P.lrho, P.lbeta);
     }
 }
 
 template <int DIM>
-__device__ __forceinline__ Prim<float, DIM> prim_load(const float4 *s) {
+__device__ __forceinline__ Prim<float, DIM> prim_load(const float4 *pa, const float4 *pb) {
     Prim<float, DIM> P;
-    const float4 a = s[0], b = s[1];
+    const float4 a = *pa, b = *pb;
     P.rho = a.x;
     P.v[0] = a.y;
     P.v[1] = a.z;
@@ -113,17 +149,21 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // Node work table (shared, one row per node q of the element):
-//   pd[t]    pair t of this thread: qa | qb << 8 | k << 16
+//   pd[t]    pair t of this thread: slot(qa) | slot(qb) << 8 | k << 16
+//   pw[t]    pair-flux slot that pair t is written to
 //   aslot[k] three 10-bit pair-flux slots accumulated by node q along k
 //   fslot[k] face slot of node q along k, or -1
-//   sfd[t]   face slot t of this thread: face | own node << 8 | neighbour node << 16
+//   sfd[t]   face slot t of this thread: face | slot(own face node) << 8 | neighbour's node << 16
+//   qsl      slot of node q
 //   acoef    2 D_{q m} for the three other nodes m of each line
 template <int DIM>
 struct NodeTable {
     int pd[BoxShape<DIM>::PPT];
+    int pw[BoxShape<DIM>::PPT];
     int aslot[DIM];
     int fslot[DIM];
     int sfd[BoxShape<DIM>::FPT];
+    int qsl;
     float acoef[DIM][3];
 };
 
@@ -147,7 +187,8 @@ __device__ __forceinline__ void build_node_table(NodeTable<DIM> &T, int q, const
             qa = k == 0 ? a + 4 * l0 + 16 * l1 : (k == 1 ? l0 + 4 * a + 16 * l1 : l0 + 4 * l1 + 16 * a);
             qb = k == 0 ? b + 4 * l0 + 16 * l1 : (k == 1 ? l0 + 4 * b + 16 * l1 : l0 + 4 * l1 + 16 * b);
         }
-        T.pd[t] = qa | (qb << 8) | (k << 16);
+        T.pd[t] = node_slot<DIM>(qa) | (node_slot<DIM>(qb) << 8) | (k << 16);
+        T.pw[t] = pair_slot<DIM>(pp < B::NPAIR ? pp : 0);
     }
 #pragma unroll
     for (int k = 0; k < DIM; ++k) {
@@ -160,7 +201,7 @@ __device__ __forceinline__ void build_node_table(NodeTable<DIM> &T, int q, const
             const int m = c < ik ? c : c + 1;   // the c-th node of the line other than q
             const int lo = m < ik ? m : ik, hi = m < ik ? ik : m;
             const int lp = lo == 0 ? hi - 1 : (lo == 1 ? hi + 1 : 5);
-            sl |= (k * LPD + line * 6 + lp) << (10 * c);
+            sl |= pair_slot<DIM>(k * LPD + line * 6 + lp) << (10 * c);
             T.acoef[k][c] = 2.0f * Df[ik * 4 + m];
         }
         T.aslot[k] = sl;
@@ -170,8 +211,9 @@ __device__ __forceinline__ void build_node_table(NodeTable<DIM> &T, int q, const
     for (int t = 0; t < B::FPT; ++t) {
         const int sl = q + NP * t;
         const int f = sl / NFP, kk = sl % NFP;
-        T.sfd[t] = f | (face_node_dev<DIM>(f, kk) << 8) | (face_node_dev<DIM>(f ^ 1, kk) << 16);
+        T.sfd[t] = f | (node_slot<DIM>(face_node_dev<DIM>(f, kk)) << 8) | (face_node_dev<DIM>(f ^ 1, kk) << 16);
     }
+    T.qsl = node_slot<DIM>(q);
 }
 
 // FP32 stage row U_n + a1 K_1 + asub K_{i-1} at one node, from global memory
@@ -197,8 +239,9 @@ struct BoxSmem {
     static constexpr int NP = B::NP, V = B::V, X = B::X;
     static constexpr int NOWN = PIPE ? 5 * V + 1 : 1;   // staging: own [U | K_1 | K_{i-1} | d hi | d lo] x V, omega J
     static constexpr int NNB = PIPE ? 3 * V : 1;        // staging: neighbour face node [U | K_1 | K_{i-1}] x V
-    float4 pr[EPB][NP][2];
-    float4 u[EPB][NP];
+    float4 pa[EPB][NP], pb[EPB][NP];   // primitives, node n at node_slot(n)
+    float4 u[EPB][NP];                 // state, node n at node_slot(n)
+    // (pair fluxes: pair pp at pair_slot(pp))
     float u5[EPB][X ? NP : 1];
     float4 pf[EPB][B::NPAIR];
     float pf5[EPB][X ? B::NPAIR : 1];
@@ -215,11 +258,11 @@ constexpr size_t stage_box_smem_bytes() {
     return sizeof(BoxSmem<DIM, EPB, PIPE>);
 }
 
-// Register budget per thread: ~48 in 2D without staging (10 CTAs of 128
+// Register budget per thread: 40 in 2D without staging (12 CTAs of 128
 // threads), ~72 with staging, ~96 in 3D.
 template <int DIM, int EPB, bool PIPE>
 constexpr int box_min_blocks() {
-    return DIM == 2 ? ((PIPE ? 896 : 1280) / (EPB * ipow4(DIM)) > 0 ? (PIPE ? 896 : 1280) / (EPB * ipow4(DIM)) : 1)
+    return DIM == 2 ? ((PIPE ? 896 : 1536) / (EPB * ipow4(DIM)) > 0 ? (PIPE ? 896 : 1536) / (EPB * ipow4(DIM)) : 1)
                     : (EPB * ipow4(DIM) <= 128 ? 640 / (EPB * ipow4(DIM)) : 2);
 }
 
@@ -345,8 +388,9 @@ __global__ void __launch_bounds__(EPB * ipow4(DIM), box_min_blocks<DIM, EPB, PIP
         const float jak[3] = {geo.x, geo.y, geo.z};
         const float invJ = geo.w;
         const Prim<float, DIM> pr = make_prim<float, DIM>(u, gm1, bad);
-        prim_store<DIM>(S.pr[el][q], pr);
-        vec_store<V>(&S.u[el][q], &S.u5[el][X ? q : 0], u);
+        const int qsl = T.qsl;
+        prim_store<DIM>(&S.pa[el][qsl], &S.pb[el][qsl], pr);
+        vec_store<V>(&S.u[el][qsl], &S.u5[el][X ? qsl : 0], u);
         __syncthreads();
         if constexpr (PIPE) {
             if (gn < ngroups) issue(e_n, nb_n);   // the staging columns are free
@@ -362,9 +406,10 @@ __global__ void __launch_bounds__(EPB * ipow4(DIM), box_min_blocks<DIM, EPB, PIP
             if (sl < NSF) {
                 const int sfd = T.sfd[t];
                 const int f = sfd & 0xff, k = f >> 1, qs = (sfd >> 8) & 0xff;
-                const Prim<float, DIM> ps = prim_load<DIM>(S.pr[el][qs]);
+                const int qss = qs;   // already a slot
+                const Prim<float, DIM> ps = prim_load<DIM>(&S.pa[el][qss], &S.pb[el][qss]);
                 float us[V];
-                vec_load<V>(&S.u[el][qs], &S.u5[el][X ? qs : 0], us);
+                vec_load<V>(&S.u[el][qss], &S.u5[el][X ? qss : 0], us);
                 const Prim<float, DIM> pn = make_prim<float, DIM>(un[t], gm1, bad);
                 const float fnv = __ldg(P.fnorm_f + (size_t)e * NF + f);
                 // canonical order f*(U_plus_side, U_minus_side): both elements of
@@ -398,8 +443,9 @@ __global__ void __launch_bounds__(EPB * ipow4(DIM), box_min_blocks<DIM, EPB, PIP
             const int pp = q + NP * t;
             if (pp < NPAIR) {
                 const int pd = T.pd[t];
-                const Prim<float, DIM> A = prim_load<DIM>(S.pr[el][pd & 0xff]);
-                const Prim<float, DIM> Bq = prim_load<DIM>(S.pr[el][(pd >> 8) & 0xff]);
+                const int sa = pd & 0xff, sb = (pd >> 8) & 0xff;
+                const Prim<float, DIM> A = prim_load<DIM>(&S.pa[el][sa], &S.pb[el][sa]);
+                const Prim<float, DIM> Bq = prim_load<DIM>(&S.pa[el][sb], &S.pb[el][sb]);
                 const int k = pd >> 16;
                 float jk = jak[0];
 #pragma unroll
@@ -408,7 +454,8 @@ __global__ void __launch_bounds__(EPB * ipow4(DIM), box_min_blocks<DIM, EPB, PIP
 #pragma unroll
                 for (int a = 0; a < DIM; ++a) nv[a] = (a == k) ? jk : 0.0f;
                 ranocha<float, DIM, -1>(A, Bq, nv, inv_gm1, F);
-                vec_store<V>(&S.pf[el][pp], &S.pf5[el][X ? pp : 0], F);
+                const int pw = T.pw[t];
+                vec_store<V>(&S.pf[el][pw], &S.pf5[el][X ? pw : 0], F);
             }
         }
         __syncthreads();
