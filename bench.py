@@ -141,12 +141,14 @@ def reduce_over_ranks(x, world, op):
     return float(t.item())
 
 
-# DRAM traffic of the roofline kernel (all-active stage of the batched 2D
-# workload, generic mixed stage kernel) from one ncu capture of the full-size
+# DRAM traffic of the roofline kernel (all-active last stage of the batched 2D
+# workload) per stage kernel variant, from one ncu capture of each full-size
 # launch (profiles/k_stage_batched2d_traffic.md).  It is reported only while
-# the stage kernel sources are the ones that capture measured.
-STAGE_TRAFFIC = {"workload": "batched2d", "stage_variant": 0, "bytes": 2431864064 + 1228096000,
-                 "sources_sha256": "4d75f7c498b7f591ff8b1ac6b7c697afa9394fc845d30525bdee5c13cf58c7cc"}
+# the stage kernel sources are the ones those captures measured.
+STAGE_TRAFFIC = {"workload": "batched2d",
+                 "bytes": {0: 1597560576 + 1228000768,      # generic kernel, 8 elements per CTA
+                           1: 1599218176 + 1246693376},     # box kernel, 16 elements per CTA
+                 "sources_sha256": "4a1197065d940fbb6f9aea0c8ebb2f039f03b020e53ce6b9fa42fb65b90caff0"}
 STAGE_SOURCES = ["stage.cuh", "stage_box.cuh", "physics.cuh", "dfloat.cuh", "kernels_stage2d.cu", "stage_launch.cu"]
 
 
@@ -156,9 +158,9 @@ def stage_traffic(workload, variant):
     for f in STAGE_SOURCES:
         with open(os.path.join(ROOT, "paper_2507_04991_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
-    ok = (workload == STAGE_TRAFFIC["workload"] and variant == STAGE_TRAFFIC["stage_variant"]
+    ok = (workload == STAGE_TRAFFIC["workload"] and variant in STAGE_TRAFFIC["bytes"]
           and h.hexdigest() == STAGE_TRAFFIC["sources_sha256"])
-    return STAGE_TRAFFIC["bytes"] if ok else None
+    return STAGE_TRAFFIC["bytes"][variant] if ok else None
 
 
 def measured_peaks():
