@@ -21,6 +21,18 @@ after max_it passes; if it did not stop by one of the
 two tolerances, or gamma is not in (0.5, 1.5), take gamma = 1 (Sec. 3.2,
 fallback of Sec. 3.2.1).  Relaxed update (eq. RRKM_Update):
 U_{n+1} = U_n + gamma dt d, t_{n+1} = t_n + gamma dt.
+
+The two other root finders the paper considers (Sec. 3.1), one evaluation of
+r per full-state pass:
+  bisection: r at the bracket ends [lo, hi] (Sec. 4.2 takes [0.8, 1.2]),
+  which must differ in sign, then at midpoints, keeping the half whose ends
+  differ in sign; stop on |r(mid)| <= tol_r A_n or a bracket of length
+  <= tol_g (take that midpoint) or after max_it passes;
+  secant: the two initial guesses lo and hi, then
+  g_{k+1} = g_k - r_k (g_k - g_{k-1}) / (r_k - r_{k-1}); stop on
+  |r_k| <= tol_r A_n or |g_{k+1} - g_k| <= tol_g (take g_k) or after max_it.
+Both take an evaluated point, so H_{n+1} is that evaluation; the same
+fallback applies.
 """
 import dataclasses
 
@@ -29,6 +41,7 @@ import numpy as np
 from . import dgsem, physics, tableau
 
 GUESS_ONE, GUESS_PREV = "one", "prev"
+SOLVER_NEWTON, SOLVER_BISECTION, SOLVER_SECANT = "newton", "bisection", "secant"
 TARGET_DELTA_H, TARGET_PREV, TARGET_INITIAL = "delta_h", "prev", "initial"
 
 
@@ -40,6 +53,9 @@ class NewtonOptions:
     guess: str = GUESS_PREV
     target: str = TARGET_DELTA_H
     relax: bool = True
+    solver: str = SOLVER_NEWTON
+    lo: float = 0.8          # bisection bracket / secant initial guesses
+    hi: float = 1.2
 
 
 @dataclasses.dataclass
@@ -115,6 +131,10 @@ class Solver:
         else:
             tgt = lambda g: self.H0
             dtgt = 0.0
+        if o.solver == SOLVER_BISECTION:
+            return self._bisection(U, d, dt, A_n, tgt)
+        if o.solver == SOLVER_SECANT:
+            return self._secant(U, d, dt, A_n, tgt)
         g = guess
         converged = False
         it = 0
@@ -140,6 +160,72 @@ class Solver:
         if not converged or not np.isfinite(g) or not (0.5 < g < 1.5):
             return 1.0, it, False
         return g, it, True
+
+    def _residual(self, U, d, dt, tgt, g):
+        return self.entropy(U + g * dt * d) - tgt(g)
+
+    @staticmethod
+    def _accept(g, converged, it):
+        if not converged or not np.isfinite(g) or not (0.5 < g < 1.5):
+            return 1.0, it, False
+        return g, it, True
+
+    def _bisection(self, U, d, dt, A_n, tgt):
+        o = self.opts
+        lo, hi = o.lo, o.hi
+        it = 0
+        r_lo = r_hi = None
+        while it < o.max_it:
+            if r_lo is None:
+                g = lo
+            elif r_hi is None:
+                g = hi
+            else:
+                g = 0.5 * (lo + hi)
+            r = self._residual(U, d, dt, tgt, g)
+            it += 1
+            if not np.isfinite(r):
+                return self._accept(g, False, it)
+            if abs(r) <= o.tol_r * A_n:
+                return self._accept(g, True, it)
+            if r_lo is None:
+                r_lo = r
+            elif r_hi is None:
+                r_hi = r
+                if not (r_lo * r_hi < 0.0):        # no sign change: no bracketed root
+                    return self._accept(g, False, it)
+            else:
+                if r * r_lo < 0.0:
+                    hi, r_hi = g, r
+                else:
+                    lo, r_lo = g, r
+                if hi - lo <= o.tol_g:
+                    return self._accept(g, True, it)
+        return self._accept(lo, False, it)
+
+    def _secant(self, U, d, dt, A_n, tgt):
+        o = self.opts
+        g_prev, r_prev = None, None
+        g = o.lo
+        it = 0
+        while it < o.max_it:
+            r = self._residual(U, d, dt, tgt, g)
+            it += 1
+            if not np.isfinite(r):
+                return self._accept(g, False, it)
+            if abs(r) <= o.tol_r * A_n:
+                return self._accept(g, True, it)
+            if g_prev is None:
+                g_prev, r_prev, g = g, r, o.hi
+                continue
+            den = r - r_prev
+            if den == 0.0:
+                return self._accept(g, False, it)
+            g_new = g - r * (g - g_prev) / den
+            if abs(g_new - g) <= o.tol_g:
+                return self._accept(g, True, it)
+            g_prev, r_prev, g = g, r, g_new
+        return self._accept(g, False, it)
 
     def step(self, dt):
         U = self.U

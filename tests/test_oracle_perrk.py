@@ -126,3 +126,66 @@ def test_newton_fallback():
     s = perrk.Solver(wl, perrk.NewtonOptions(max_it=1, tol_r=0.0, tol_g=0.0))
     rec = s.step(wl.dt)
     assert rec.gamma == 1.0 and not rec.converged and rec.iters == 1
+
+
+def _burgers_root_case():
+    wl = workloads.burgers_1d()
+    s = perrk.Solver(wl)
+    U = s.U.copy()
+    dt = wl.dt * 2
+    d, dH, _ = s.stages(U, dt)
+    ud = s.geo.integrate(U[0] * d[0])
+    dd = s.geo.integrate(d[0] * d[0])
+    g_cf = 2.0 * (dH - dt * ud) / (dt * dt * dd)
+    return wl, dt, g_cf
+
+
+def test_bisection_pass_count_and_bracket():
+    """Bisection (Sec. 3.1) on [0.8, 1.2] with only the bracket-length stop:
+    2 end evaluations, then k halvings with 0.4 / 2^k <= tol_g, and the root
+    within tol_g of the accepted midpoint (closed-form root of the quadratic
+    entropy)."""
+    wl, dt, g_cf = _burgers_root_case()
+    tol_g = 1e-6
+    k = math.ceil(math.log2(0.4 / tol_g))
+    s = perrk.Solver(wl, perrk.NewtonOptions(solver=perrk.SOLVER_BISECTION, tol_r=0.0, tol_g=tol_g, max_it=60))
+    rec = s.step(dt)
+    assert rec.converged and rec.iters == 2 + k
+    assert abs(rec.gamma - g_cf) <= tol_g
+    # bracket without a sign change: no root to bisect, fallback gamma = 1
+    s = perrk.Solver(wl, perrk.NewtonOptions(solver=perrk.SOLVER_BISECTION, lo=g_cf + 0.1, hi=g_cf + 0.2))
+    rec = s.step(dt)
+    assert not rec.converged and rec.gamma == 1.0 and rec.iters == 2
+
+
+def test_secant_and_newton_reach_the_closed_form_root():
+    """Secant from the two guesses 0.8, 1.2 and Newton from 1 converge to the
+    closed-form root of the quadratic entropy; the secant takes a handful of
+    passes (superlinear), bisection to the same tolerance dozens."""
+    wl, dt, g_cf = _burgers_root_case()
+    res = {}
+    for solver in (perrk.SOLVER_NEWTON, perrk.SOLVER_SECANT, perrk.SOLVER_BISECTION):
+        s = perrk.Solver(wl, perrk.NewtonOptions(solver=solver, guess=perrk.GUESS_ONE, tol_r=1e-15, tol_g=1e-13,
+                                                 max_it=80))
+        rec = s.step(dt)
+        assert rec.converged, solver
+        res[solver] = rec
+    for solver, rec in res.items():
+        assert abs(rec.gamma - g_cf) < 1e-9, (solver, rec.gamma, g_cf)
+    assert res[perrk.SOLVER_SECANT].iters <= 8
+    assert res[perrk.SOLVER_BISECTION].iters > 3 * res[perrk.SOLVER_SECANT].iters
+
+
+def test_root_finders_agree_euler():
+    """Euler (KHI, ES fluxes): the three root finders give the same gamma
+    within their tolerances over several steps."""
+    wl = workloads.small_box_2d(n=6, seed=7, R=2, E=[6, 3], order=3, ic="khi")
+    wl.dt *= 3
+    gammas = {}
+    for solver in (perrk.SOLVER_NEWTON, perrk.SOLVER_SECANT, perrk.SOLVER_BISECTION):
+        s = perrk.Solver(wl, perrk.NewtonOptions(solver=solver, tol_r=1e-15, tol_g=1e-12, max_it=80))
+        gammas[solver] = [s.step(wl.dt).gamma for _ in range(3)]
+    g0 = np.array(gammas[perrk.SOLVER_NEWTON])
+    assert np.all(np.abs(g0 - 1.0) > 1e-9)
+    for solver in (perrk.SOLVER_SECANT, perrk.SOLVER_BISECTION):
+        assert np.max(np.abs(np.array(gammas[solver]) - g0)) < 1e-8, solver
