@@ -56,6 +56,13 @@ typedef enum { PERRK_SURFACE_EC = 0, PERRK_SURFACE_ES_RUSANOV = 1 } perrk_surfac
 typedef enum { PERRK_FP64 = 0, PERRK_MIXED = 1 } perrk_precision;
 typedef enum { PERRK_GUESS_ONE = 0, PERRK_GUESS_PREV = 1, PERRK_GUESS_MLP = 2 } perrk_guess;
 typedef enum { PERRK_TARGET_DELTA_H = 0, PERRK_TARGET_PREV = 1, PERRK_TARGET_INITIAL = 2 } perrk_target;
+/* Root finder for the relaxation equation (Sec. 3.1): Newton-Raphson with
+ * unit step from the guess; bisection on [bracket_lo, bracket_hi] (r at both
+ * ends, which must differ in sign, then midpoints; stop on |r| <= tol_r A_n,
+ * a bracket of length <= tol_g, or max_it passes); secant from the two
+ * guesses bracket_lo, bracket_hi (stop on |r| <= tol_r A_n or a step
+ * <= tol_g).  One full-state pass per evaluation of r. */
+typedef enum { PERRK_SOLVER_NEWTON = 0, PERRK_SOLVER_BISECTION = 1, PERRK_SOLVER_SECANT = 2 } perrk_solver;
 
 /* Step-status flags (perrk_step_info.flags), OR-ed over the steps of a call. */
 #define PERRK_FLAG_NEWTON_FALLBACK 0x1u   /* Newton did not converge: gamma = 1 taken (Sec. 3.2.1) */
@@ -108,6 +115,8 @@ typedef struct {
                                      stage (all archetypes), form d = sum b_i K_i once at the last stage
                                      from K_1, K_{S-1}, K_S; 0: accumulate d at every stage with b_i != 0.
                                      Same sums in the same order either way. */
+    int solver;                   /* a perrk_solver value, Newton by default */
+    double bracket_lo, bracket_hi; /* bisection bracket / secant initial guesses (default 0.8, 1.2, Sec. 4.2) */
 } perrk_options;
 
 /* Per-step record (perrk_step fills one per step when info != NULL). */
@@ -128,7 +137,7 @@ typedef struct perrk_ctx perrk_ctx;
 
 /* Fill opts with defaults: FP64, relaxed, max_it 10, tol_r 1e-14, tol_g 1e-14,
  * guess PREV (Sec. 3.1: gamma_{n-1}, 1 at the first step), target DELTA_H, no
- * graph, fused direction. */
+ * graph, fused direction, Newton with bracket [0.8, 1.2] for the others. */
 void perrk_default_options(perrk_options *opts);
 
 /* Validate and copy mesh and scheme, compute LGL tables and metric terms,

@@ -26,6 +26,7 @@ SURFACE_EC, SURFACE_ES_RUSANOV = 0, 1
 FP64, MIXED = 0, 1
 GUESS_ONE, GUESS_PREV, GUESS_MLP = 0, 1, 2
 TARGET_DELTA_H, TARGET_PREV, TARGET_INITIAL = 0, 1, 2
+SOLVER_NEWTON, SOLVER_BISECTION, SOLVER_SECANT = 0, 1, 2
 FLAG_NEWTON_FALLBACK, FLAG_NONPHYSICAL, FLAG_NONFINITE = 1, 2, 4
 
 EXPORTED = [
@@ -50,7 +51,8 @@ class perrk_scheme_desc(C.Structure):
 class perrk_options(C.Structure):
     _fields_ = [("precision", C.c_int), ("relaxation", C.c_int), ("newton_max_it", C.c_int),
                 ("newton_tol_r", C.c_double), ("newton_tol_g", C.c_double), ("guess", C.c_int),
-                ("target", C.c_int), ("use_graph", C.c_int), ("fuse_direction", C.c_int)]
+                ("target", C.c_int), ("use_graph", C.c_int), ("fuse_direction", C.c_int), ("solver", C.c_int),
+                ("bracket_lo", C.c_double), ("bracket_hi", C.c_double)]
 
 
 class perrk_step_info(C.Structure):
@@ -414,7 +416,7 @@ SURFACE_CODES = {"ec": SURFACE_EC, "es": SURFACE_ES_RUSANOV, "es_rusanov": SURFA
 
 
 def options(precision=FP64, relaxation=True, max_it=10, tol_r=1e-14, tol_g=1e-14, guess=GUESS_PREV,
-            target=TARGET_DELTA_H, use_graph=False, fuse_direction=True):
+            target=TARGET_DELTA_H, use_graph=False, fuse_direction=True, solver=SOLVER_NEWTON, bracket=(0.8, 1.2)):
     o = perrk_default_options()
     o.precision = precision
     o.relaxation = int(bool(relaxation))
@@ -425,6 +427,8 @@ def options(precision=FP64, relaxation=True, max_it=10, tol_r=1e-14, tol_g=1e-14
     o.target = target
     o.use_graph = int(bool(use_graph))
     o.fuse_direction = int(bool(fuse_direction))
+    o.solver = solver
+    o.bracket_lo, o.bracket_hi = float(bracket[0]), float(bracket[1])
     return o
 
 

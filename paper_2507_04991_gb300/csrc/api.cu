@@ -163,7 +163,8 @@ static perrk_status enqueue_step(Ctx &c, cudaStream_t st) {
     for (int i = 0; i < c.S; ++i) PERRK_TRY(launch_stage(c, i, false, nullptr, nullptr, nullptr, nullptr, st));
     PERRK_TRY(launch_relax_init(c, st));
     if (c.opt.relaxation) {
-        if (c.opt.guess == PERRK_GUESS_MLP && c.mlp_on) PERRK_TRY(launch_mlp_guess(c, st));
+        if (c.opt.guess == PERRK_GUESS_MLP && c.mlp_on && c.opt.solver == PERRK_SOLVER_NEWTON)
+            PERRK_TRY(launch_mlp_guess(c, st));
         for (int it = 0; it < c.opt.newton_max_it; ++it) PERRK_TRY(launch_newton_pass(c, st));
     }
     return launch_update(c, 0, st);
@@ -186,6 +187,9 @@ void perrk_default_options(perrk_options *o) {
     o->target = PERRK_TARGET_DELTA_H;
     o->use_graph = 0;
     o->fuse_direction = 1;
+    o->solver = PERRK_SOLVER_NEWTON;
+    o->bracket_lo = 0.8;
+    o->bracket_hi = 1.2;
 }
 
 perrk_status perrk_create_batched(int n, const perrk_mesh_desc *mesh, const perrk_scheme_desc *scheme,
@@ -504,7 +508,9 @@ perrk_status perrk_stage_info(const perrk_ctx *h, int stage, int64_t *n_active, 
         int k = 0;
         for (int i = 0; i < c.S; ++i) k += c.n_active[i] > 0 ? 1 : 0;
         k += 2;  // relax_init + update
-        if (c.opt.relaxation) k += c.opt.newton_max_it + ((c.opt.guess == PERRK_GUESS_MLP && c.mlp_on) ? 1 : 0);
+        if (c.opt.relaxation)
+            k += c.opt.newton_max_it +
+                 ((c.opt.guess == PERRK_GUESS_MLP && c.mlp_on && c.opt.solver == PERRK_SOLVER_NEWTON) ? 1 : 0);
         *kernels_per_step = k;
     }
     if (dof_stage_per_step) {

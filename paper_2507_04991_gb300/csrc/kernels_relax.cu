@@ -39,8 +39,8 @@ struct RelaxParams {
     int rec_slot, rec_cap, n_inst;
     size_t NE;
     double gamma_gas;
-    int max_it, guess, target, relax, query, mixed;
-    double tol_r, tol_g;
+    int max_it, guess, target, relax, query, mixed, solver;
+    double tol_r, tol_g, br_lo, br_hi;
     const float4 *dftab;    // double-float log table (mixed form)
     DfConst K;
 };
@@ -228,6 +228,12 @@ __global__ void k_relax_init(const RelaxParams P) {
         return;
     }
     S.gamma = (P.guess == PERRK_GUESS_ONE) ? 1.0 : S.hist_gamma[0];
+    if (P.solver != PERRK_SOLVER_NEWTON) {
+        // bisection: first pass at the bracket's lower end; secant: first guess
+        S.br_lo = P.br_lo;
+        S.br_hi = P.br_hi;
+        S.gamma = P.br_lo;
+    }
     S.gamma_guess = S.gamma;
     S.gamma_eval = NAN;
     S.done = 0;
@@ -317,7 +323,68 @@ __global__ void __launch_bounds__(256) k_newton_pass(const RelaxParams P) {
     S.R_last = R;
     S.G_last = G;
     S.A_last = A;
-    if (fabs(r) <= P.tol_r * S.A_n) {
+    if (P.solver == PERRK_SOLVER_BISECTION) {
+        // Sec. 3.1 bisection: r at lo, at hi (must differ in sign), then midpoints
+        const double g = S.gamma;
+        if (!isfinite(r)) {
+            S.done = 1;
+        } else if (fabs(r) <= P.tol_r * S.A_n) {
+            S.converged = 1;
+            S.done = 1;
+        } else if (S.iters == 1) {
+            S.r_lo = r;
+            S.gamma = S.br_hi;
+        } else if (S.iters == 2) {
+            S.r_hi = r;
+            if (!(S.r_lo * r < 0.0)) S.done = 1;   // no sign change: no bracketed root
+            else S.gamma = 0.5 * (S.br_lo + S.br_hi);
+        } else {
+            if (r * S.r_lo < 0.0) {
+                S.br_hi = g;
+                S.r_hi = r;
+            } else {
+                S.br_lo = g;
+                S.r_lo = r;
+            }
+            if (S.br_hi - S.br_lo <= P.tol_g) {
+                S.converged = 1;                    // take the evaluated midpoint
+                S.done = 1;
+            } else {
+                S.gamma = 0.5 * (S.br_lo + S.br_hi);
+            }
+        }
+    } else if (P.solver == PERRK_SOLVER_SECANT) {
+        // Sec. 3.1 secant from the two guesses br_lo, br_hi
+        const double g = S.gamma;
+        if (!isfinite(r)) {
+            S.done = 1;
+        } else if (fabs(r) <= P.tol_r * S.A_n) {
+            S.converged = 1;
+            S.done = 1;
+        } else if (S.iters == 1) {
+            S.g_prev = g;
+            S.r_prev = r;
+            S.gamma = S.br_hi;
+        } else {
+            const double den = r - S.r_prev;
+            if (den == 0.0) {
+                S.done = 1;
+            } else {
+                const double g_new = g - r * (g - S.g_prev) / den;
+                if (fabs(g_new - g) <= P.tol_g) {
+                    S.converged = 1;                // take the evaluated g
+                    S.done = 1;
+                } else {
+                    S.g_prev = g;
+                    S.r_prev = r;
+                    S.gamma = g_new;
+                }
+            }
+        }
+        if (!S.done && S.iters >= P.max_it) S.done = 1;
+        if (S.done) accept_gamma(S);
+        return;
+    } else if (fabs(r) <= P.tol_r * S.A_n) {
         // no further pass; the correction from this pass is still applied
         if (isfinite(r) && isfinite(rp) && rp != 0.0) S.gamma = S.gamma - r / rp;
         S.converged = 1;
@@ -552,6 +619,9 @@ static RelaxParams relax_params(Ctx &c) {
     P.mixed = c.opt.precision == PERRK_MIXED ? 1 : 0;
     P.tol_r = c.opt.newton_tol_r;
     P.tol_g = c.opt.newton_tol_g;
+    P.solver = c.opt.solver;
+    P.br_lo = c.opt.bracket_lo;
+    P.br_hi = c.opt.bracket_hi;
     P.dftab = (const float4 *)c.g_dftab;
     P.K.ln2 = df{c.df_consts[0], c.df_consts[1]};
     P.K.third = df{c.df_consts[2], c.df_consts[3]};

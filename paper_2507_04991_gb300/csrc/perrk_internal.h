@@ -69,6 +69,9 @@ struct InstScalars {
     double hist_dh[3];     // (Delta H / A)_{n}, _{n-1}, _{n-2} after the step
     double H_next;
     double feat[6];        // learned-guess features of the current step
+    double br_lo, br_hi;   // bisection bracket
+    double r_lo, r_hi;     // residuals at the bracket ends (r_hi unset until the second pass)
+    double g_prev, r_prev; // secant: previous iterate and residual
     int32_t iters;
     int32_t done;
     int32_t converged;

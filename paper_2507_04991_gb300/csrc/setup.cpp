@@ -103,6 +103,10 @@ perrk_status build_ctx(Ctx &c, int n, const perrk_mesh_desc *mesh, const perrk_s
     if (opts->newton_max_it < 0 || opts->newton_max_it > 64) return fail("newton_max_it out of range [0, 64]");
     if (!(opts->newton_tol_r >= 0.0) || !(opts->newton_tol_g >= 0.0)) return fail("negative Newton tolerance");
     if (opts->guess < 0 || opts->guess > 2 || opts->target < 0 || opts->target > 2) return fail("bad guess/target enum");
+    if (opts->solver < 0 || opts->solver > 2) return fail("unknown relaxation solver");
+    if (opts->solver != PERRK_SOLVER_NEWTON &&
+        !(std::isfinite(opts->bracket_lo) && std::isfinite(opts->bracket_hi) && opts->bracket_lo < opts->bracket_hi))
+        return fail("bisection / secant need finite bracket_lo < bracket_hi");
 
     c.dim = dim;
     c.NP = ipow4(dim);

@@ -90,3 +90,15 @@ def test_status_strings(lib):
     assert pk.status_string(0) == "ok"
     assert pk.status_string(3) == "non-physical state"
     assert pk.perrk_mlp_size() == 64 * 6 + 64 + 64 * 64 + 64 + 64 + 1 + 2 * 6 + 1
+
+
+@pytest.mark.parametrize("bad", ["solver", "bracket"])
+def test_invalid_solver_options_rejected(lib, bad):
+    wl, keep, m, (c, b, a1, asub) = _small_mesh()
+    s = pk.scheme_desc(3, [6, 3], c, b, a1, asub, pk.EULER_2D, pk.SURFACE_ES_RUSANOV, 1.4, keep)
+    o = pk.options(solver=pk.SOLVER_BISECTION, bracket=(1.2, 0.8)) if bad == "bracket" else pk.options()
+    if bad == "solver":
+        o.solver = 7
+    with pytest.raises(pk.PerrkError) as ei:
+        pk.perrk_create(m, s, o)
+    assert ei.value.status == pk.PERRK_INVALID_ARG

@@ -50,9 +50,9 @@ def gamma_explained_tol(grec, rrec, u_ref, base=1e-12):
 
 
 def gpu_run(wl, nsteps, precision=pk.FP64, relax=True, max_it=10, tol_r=1e-14, tol_g=1e-14, guess=pk.GUESS_PREV,
-            target=pk.TARGET_DELTA_H, use_graph=False):
+            target=pk.TARGET_DELTA_H, use_graph=False, solver=pk.SOLVER_NEWTON, bracket=(0.8, 1.2)):
     opts = pk.options(precision=precision, relaxation=relax, max_it=max_it, tol_r=tol_r, tol_g=tol_g, guess=guess,
-                      target=target, use_graph=use_graph)
+                      target=target, use_graph=use_graph, solver=solver, bracket=bracket)
     s = pk.Solver(wl, opts)
     recs = s.step(nsteps)
     u = s.state()
@@ -238,3 +238,46 @@ def test_nonphysical_state_reported():
         s.step(1)
     assert ei.value.status == pk.PERRK_NONPHYSICAL_STATE
     s.close()
+
+
+SOLVERS = {pk.SOLVER_BISECTION: "bisection", pk.SOLVER_SECANT: "secant"}
+
+
+@pytest.mark.parametrize("precision", [pk.FP64, pk.MIXED])
+@pytest.mark.parametrize("solver", [pk.SOLVER_BISECTION, pk.SOLVER_SECANT])
+def test_root_finder_parity(solver, precision):
+    """Bisection and secant relaxation solvers (Sec. 3.1) against the oracle
+    with the same rules: gamma per step and the pass counts (float64), the
+    state at the usual bars; in a CUDA graph."""
+    wl = workloads.small_box_2d(n=8, seed=59, R=2, E=[6, 3], order=3, ic="khi")
+    wl.dt *= 3
+    kw = dict(max_it=60, tol_r=1e-15, tol_g=1e-12)
+    ref, rrec = oracle_run(wl, 5, solver=SOLVERS[solver], **kw)
+    u, grec = gpu_run(wl, 5, precision=precision, solver=solver, use_graph=True, **kw)
+    for a, b in zip(grec, rrec):
+        assert a["flags"] & pk.FLAG_NEWTON_FALLBACK == 0 and b.converged
+        assert abs(a["gamma"] - b.gamma) < (1e-9 if precision == pk.FP64 else 5e-4)
+        if precision == pk.FP64:
+            assert abs(a["iters"] - b.iters) <= 1
+    tol = gamma_explained_tol(grec, rrec, ref.U) if precision == pk.FP64 else TOL[precision]
+    assert rel_linf(u, ref.U) < tol
+
+
+def test_bisection_closed_form_root_and_bracket_fallback():
+    """Burgers (quadratic entropy): GPU bisection with only the bracket-length
+    stop takes 2 + ceil(log2(0.4 / tol_g)) passes and lands within tol_g of the
+    closed-form root; a bracket without a sign change falls back to gamma = 1."""
+    import math
+    wl = workloads.burgers_1d()
+    wl.dt *= 2
+    s = operrk.Solver(wl)
+    d, dH, _ = s.stages(s.U.copy(), wl.dt)
+    ud = s.geo.integrate(s.U[0] * d[0])
+    dd = s.geo.integrate(d[0] * d[0])
+    g_cf = 2.0 * (dH - wl.dt * ud) / (wl.dt * wl.dt * dd)
+    tol_g = 1e-6
+    _, grec = gpu_run(wl, 1, solver=pk.SOLVER_BISECTION, max_it=60, tol_r=0.0, tol_g=tol_g)
+    assert grec[0]["iters"] == 2 + math.ceil(math.log2(0.4 / tol_g))
+    assert abs(grec[0]["gamma"] - g_cf) <= tol_g
+    _, grec = gpu_run(wl, 1, solver=pk.SOLVER_BISECTION, bracket=(g_cf + 0.1, g_cf + 0.2))
+    assert grec[0]["flags"] & pk.FLAG_NEWTON_FALLBACK and grec[0]["gamma"] == 1.0 and grec[0]["iters"] == 2
