@@ -113,15 +113,25 @@ class ClockSampler:
                 "power_w_max": max(pw) if pw else None, "reasons": sorted(reasons), "samples": len(self.samples)}
 
 
-def dist_setup():
+_BACKEND = None
+
+
+def dist_setup(backend=None):
+    """Ranks from the torch.distributed.run environment; NCCL on GPUs, gloo
+    on CPU (replica bookkeeping only: the data path has no collective)."""
+    global _BACKEND
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+        if backend is None:
+            backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+        _BACKEND = backend
     return world, rank, local
 
 
@@ -132,11 +142,12 @@ def barrier(world):
 
 
 def reduce_over_ranks(x, world, op):
+    """Max or sum of a host scalar over the ranks."""
     if world <= 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if _BACKEND == "nccl" else "cpu")
     dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
     return float(t.item())
 
