@@ -418,8 +418,34 @@ __global__ void __launch_bounds__(256) k_update(const RelaxParams P) {
     df R = {0.0f, 0.0f};
     float A = 0.0f, G = 0.0f;
     const df gdtf = df_from(gdt);
+    if constexpr (DF) {
+        if (!needH) {
+            // the common case: a pure stream over the float pairs, four
+            // consecutive nodes per thread and 16-byte accesses (chunk bounds
+            // and array offsets are multiples of NP >= 4 nodes)
+            const size_t j0 = n0 / 4, j1 = n1 / 4, NP4 = NPtot / 4;
+            float4 *Uf4 = reinterpret_cast<float4 *>(P.Uf), *Ul4 = reinterpret_cast<float4 *>(P.Ul);
+            const float4 *dh4 = reinterpret_cast<const float4 *>(P.dh), *dl4 = reinterpret_cast<const float4 *>(P.dl);
+            for (size_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    const size_t i = v * NP4 + j;
+                    const float4 uh = Uf4[i], ul = Ul4[i], dh = __ldg(dh4 + i), dl = __ldg(dl4 + i);
+                    const df x0 = df_add(df{uh.x, ul.x}, df_mul(gdtf, df{dh.x, dl.x}));
+                    const df x1 = df_add(df{uh.y, ul.y}, df_mul(gdtf, df{dh.y, dl.y}));
+                    const df x2 = df_add(df{uh.z, ul.z}, df_mul(gdtf, df{dh.z, dl.z}));
+                    const df x3 = df_add(df{uh.w, ul.w}, df_mul(gdtf, df{dh.w, dl.w}));
+                    Uf4[i] = make_float4(x0.hi, x1.hi, x2.hi, x3.hi);
+                    Ul4[i] = make_float4(x0.lo, x1.lo, x2.lo, x3.lo);
+                    if (!isfinite(x0.hi) || !isfinite(x1.hi) || !isfinite(x2.hi) || !isfinite(x3.hi))
+                        bad |= PERRK_FLAG_NONFINITE;
+                }
+            }
+        }
+    }
     for (size_t j = n0 + threadIdx.x; j < n1; j += blockDim.x) {
         if constexpr (DF) {
+            if (!needH) break;
             // U_{n+1} = U_n + gamma dt d in double-float (FP32 pipe)
             df x[V];
 #pragma unroll
