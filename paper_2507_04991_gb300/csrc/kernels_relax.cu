@@ -55,7 +55,7 @@ __device__ __forceinline__ df df_entropy(const df *x, const float *dv, const Rel
         if (dv) wd = x[0].hi * dv[0];
         return df{0.5f * sq.hi, 0.5f * sq.lo};
     } else {
-        const df ir = df_div(df{1.0f, 0.0f}, x[0]);
+        const df ir = df_rcp(x[0]);
         df m2 = df_mul(x[1], x[1]);
 #pragma unroll
         for (int a = 1; a < DIM; ++a) m2 = df_add(m2, df_mul(x[1 + a], x[1 + a]));
@@ -72,7 +72,9 @@ __device__ __forceinline__ df df_entropy(const df *x, const float *dv, const Rel
         const df S = df_sub(lp, df_mul(P.K.gam, lr));
         if (dv) {
             // w in float: (gamma - S - (gamma-1) |m|^2/(2 rho p), (gamma-1) m/p, -(gamma-1) rho/p)
-            const float gm1 = P.K.gm1.hi, ip = 1.0f / p.hi;
+            float ip;   // w only needs float accuracy
+            asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(ip) : "f"(p.hi));
+            const float gm1 = P.K.gm1.hi;
             const float w0 = P.K.gam.hi - S.hi - gm1 * ke.hi * ip;
             float md = 0.0f;
 #pragma unroll
