@@ -159,7 +159,7 @@ def reduce_over_ranks(x, world, op):
 STAGE_TRAFFIC = {"workload": "batched2d",
                  "bytes": {0: 1597560576 + 1228000768,      # generic kernel, 8 elements per CTA
                            1: 1599218176 + 1246693376},     # box kernel, 16 elements per CTA
-                 "sources_sha256": "4a1197065d940fbb6f9aea0c8ebb2f039f03b020e53ce6b9fa42fb65b90caff0"}
+                 "sources_sha256": "083b2471d6da0526e2824d0f748c55b8fcd27cceb93b2d8ed0953002058ef0b8"}
 STAGE_SOURCES = ["stage.cuh", "stage_box.cuh", "physics.cuh", "dfloat.cuh", "kernels_stage2d.cu", "stage_launch.cu"]
 
 
