@@ -281,3 +281,65 @@ def test_bisection_closed_form_root_and_bracket_fallback():
     assert abs(grec[0]["gamma"] - g_cf) <= tol_g
     _, grec = gpu_run(wl, 1, solver=pk.SOLVER_BISECTION, bracket=(g_cf + 0.1, g_cf + 0.2))
     assert grec[0]["flags"] & pk.FLAG_NEWTON_FALLBACK and grec[0]["gamma"] == 1.0 and grec[0]["iters"] == 2
+
+
+# ----------------------------------------------------------------------------- edge cases
+
+def _edge_case(name):
+    if name == "one_element":
+        # a single periodic element: every face pairs the element with itself
+        return workloads.small_box_2d(n=1, seed=61, R=1, E=[4], order=2)
+    if name == "empty_partition":
+        # member 1 of the family owns no element: its rows are never active
+        wl = workloads.small_box_2d(n=6, seed=62, R=2, E=[6, 3], order=3)
+        wl.part = np.zeros_like(wl.part)
+        return wl
+    if name == "ragged_prefix":
+        # 7 x 7 elements with random partitions: no stage prefix is a multiple
+        # of the elements per CTA
+        return workloads.small_box_2d(n=7, seed=63, R=3, E=[8, 6, 3], order=3, random_parts=True)
+    raise KeyError(name)
+
+
+@pytest.mark.parametrize("precision", [pk.FP64, pk.MIXED])
+@pytest.mark.parametrize("name", ["one_element", "empty_partition", "ragged_prefix"])
+def test_edge_case_meshes(name, precision):
+    """Degenerate and ragged inputs against the oracle: a single self-periodic
+    element, a family member without elements, and active prefixes that are
+    not multiples of the CTA's element count (every EPB choice)."""
+    wl = _edge_case(name)
+    ref, rrec = oracle_run(wl, 4)
+    tested = 0
+    for epb in (4, 8, 16):
+        opts = pk.options(precision=precision)
+        s = pk.Solver(wl, opts)
+        pk.perrk_set_tuning(s.h, epb, 0, 128, 0)
+        try:
+            recs = [r[0] for r in s.step(4)]
+        except pk.PerrkError as err:
+            # a mapping whose shared memory does not fit this precision is refused at launch
+            assert "invalid configuration" in str(err)
+            s.close()
+            continue
+        u = s.state()
+        s.close()
+        tested += 1
+        tol = gamma_explained_tol(recs, rrec, ref.U) if precision == pk.FP64 else TOL[precision]
+        assert rel_linf(u, ref.U) < tol, (name, epb, rel_linf(u, ref.U), tol)
+        for a, b in zip(recs, rrec):
+            assert abs(a["gamma"] - b.gamma) < (1e-7 if precision == pk.FP64 else 5e-4)
+    assert tested >= 2
+
+
+def test_zero_steps_and_relaxation_off():
+    """nsteps = 0 leaves the state untouched; with relaxation off gamma = 1 and
+    the step is the plain P-ERK step (oracle with relax=False)."""
+    wl = workloads.small_box_2d(n=6, seed=64, R=2, E=[6, 3], order=3)
+    s = pk.Solver(wl, pk.options())
+    pk.perrk_step(s.h, 0, info=False)
+    assert np.array_equal(s.state(), wl.u0)
+    s.close()
+    ref, rrec = oracle_run(wl, 3, relax=False)
+    u, grec = gpu_run(wl, 3, relax=False)
+    assert rel_linf(u, ref.U) < 1e-12
+    assert all(r["gamma"] == 1.0 for r in grec)
