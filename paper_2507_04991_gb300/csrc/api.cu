@@ -54,7 +54,7 @@ static perrk_status upload(T *&dst, const std::vector<T> &src, const char *what)
 }
 
 static void free_ctx(Ctx &c) {
-    void *ptrs[] = {c.U, c.K1, c.Ka, c.Kb, c.d, c.Uf, c.Ul, c.dh, c.dl, c.e_dhf, c.g_wJ_lo, c.K1f, c.Kaf, c.Kbf, c.e_dh, c.g_node, c.g_elem, c.g_fnorm, c.g_wJ, c.g_nbr, c.g_gp,
+    void *ptrs[] = {c.g_box_tab, c.U, c.K1, c.Ka, c.Kb, c.d, c.Uf, c.Ul, c.dh, c.dl, c.e_dhf, c.g_wJ_lo, c.K1f, c.Kaf, c.Kbf, c.e_dh, c.g_node, c.g_elem, c.g_fnorm, c.g_wJ, c.g_nbr, c.g_gp,
                     c.g_elist, c.g_chunk_inst, c.g_chunk_e0, c.g_chunk_e1, c.g_inst_chunk0, c.g_inst_nchunks,
                     c.g_coef, c.g_coef_f, c.g_scal, c.g_partials, c.g_counters, c.g_flags, c.g_records, c.g_mlp,
                     c.g_dftab, c.g_node_f, c.g_elem_f, c.g_fnorm_f, c.g_wJ_f};
@@ -153,6 +153,15 @@ static perrk_status alloc_ctx(Ctx &c) {
         df_tables(c.gamma_gas, tab, consts);
         PERRK_TRY(upload(c.g_dftab, tab, "df table"));
         for (int i = 0; i < 8; ++i) c.df_consts[i] = consts[i];
+    }
+    if (mixed && c.equation != PERRK_BURGERS_1D && !c.curved && c.dim >= 2) {
+        float Df[16];
+        for (int i = 0; i < 16; ++i) Df[i] = (float)c.lgl_D[i];
+        const size_t nb = c.dim == 2 ? box_node_table_2d(Df, nullptr) : box_node_table_3d(Df, nullptr);
+        std::vector<uint8_t> tab(nb);
+        if (c.dim == 2) box_node_table_2d(Df, tab.data());
+        else box_node_table_3d(Df, tab.data());
+        PERRK_TRY(upload(*reinterpret_cast<uint8_t **>(&c.g_box_tab), tab, "box table"));
     }
     c.rec_cap = 256;
     PERRK_CUDA(cudaMalloc((void **)&c.g_records, (size_t)c.rec_cap * c.n_inst * sizeof(perrk_step_info)), "records");

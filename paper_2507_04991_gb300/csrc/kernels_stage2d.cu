@@ -57,4 +57,15 @@ cudaError_t stage_launch_box_2d(const StageParams &P, int epb, bool pipe, int gr
     return cudaErrorInvalidValue;
 }
 
+// Per-node work table of the 2D box kernels, built on the host from the
+// same function the kernels were written against; bytes written to out (if
+// non-null), returns the table size.
+size_t box_node_table_2d(const float *Df, void *out) {
+    constexpr int NP = ipow4(2);
+    if (out) {
+        NodeTable<2> *T = reinterpret_cast<NodeTable<2> *>(out);
+        for (int q = 0; q < NP; ++q) build_node_table<2>(T[q], q, Df);
+    }
+    return sizeof(NodeTable<2>) * NP;
+}
 }  // namespace perrk

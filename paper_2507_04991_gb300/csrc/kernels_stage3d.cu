@@ -56,4 +56,15 @@ cudaError_t stage_launch_box_3d(const StageParams &P, int epb, bool pipe, int gr
     return cudaErrorInvalidValue;
 }
 
+// Per-node work table of the 3D box kernels, built on the host from the
+// same function the kernels were written against; bytes written to out (if
+// non-null), returns the table size.
+size_t box_node_table_3d(const float *Df, void *out) {
+    constexpr int NP = ipow4(3);
+    if (out) {
+        NodeTable<3> *T = reinterpret_cast<NodeTable<3> *>(out);
+        for (int q = 0; q < NP; ++q) build_node_table<3>(T[q], q, Df);
+    }
+    return sizeof(NodeTable<3>) * NP;
+}
 }  // namespace perrk

@@ -148,6 +148,7 @@ struct Ctx {
     int rec_cap = 0;
     float *g_mlp = nullptr;                   // weights (nullptr: no MLP)
     float *g_dftab = nullptr;                 // double-float log table [129][4]
+    void *g_box_tab = nullptr;                // box stage kernels: per-node work table
     float df_consts[8] = {0};                 // log 2, 1/3, gamma-1, gamma (float pairs)
     int mlp_on = 0;
 
@@ -188,6 +189,8 @@ perrk_status launch_update(Ctx &c, int rec_slot, void *stream);
 perrk_status launch_entropy_set(Ctx &c, void *stream);
 perrk_status launch_entropy(Ctx &c, int query, void *stream);
 perrk_status launch_mlp_guess(Ctx &c, void *stream);
+size_t box_node_table_2d(const float *Df, void *out);
+size_t box_node_table_3d(const float *Df, void *out);
 perrk_status launch_df_log(const float *tab, const float *consts, const double *x, double *y, int n, void *stream);
 perrk_status mlp_train_device(const float *feats, const float *target, int n, float *weights, int epochs,
                               float lr, float *loss, float *grad_out, void *stream);

@@ -40,6 +40,7 @@ struct StageParams {
     int d_fused;                // d = b_1 K_1 + b_m K_{S-1} + b_S K_S written once at the last stage
     int es;                     // Rusanov dissipation on the surface flux
     const float *g_node_f, *g_elem_f, *fnorm_f, *wJ_f;   // FP32 geometry (mixed form)
+    const void *box_tab;        // box kernels: per-node work table (NodeTable rows, built on the host)
     double gamma_gas;
     double D[16];
     double w_end;
@@ -71,7 +72,7 @@ struct Geo {
 };
 
 template <int DIM>
-__device__ __forceinline__ int face_pos(int q, int k) {
+__host__ __device__ __forceinline__ int face_pos(int q, int k) {
     const int i0 = q & 3, i1 = (q >> 2) & 3, i2 = (q >> 4) & 3;
     if (DIM == 1) return 0;
     if (DIM == 2) return k == 0 ? i1 : i0;
@@ -79,7 +80,7 @@ __device__ __forceinline__ int face_pos(int q, int k) {
 }
 
 template <int DIM>
-__device__ __forceinline__ int face_node_dev(int f, int kk) {
+__host__ __device__ __forceinline__ int face_node_dev(int f, int kk) {
     const int k = f >> 1, ed = (f & 1) ? 3 : 0;
     if (DIM == 1) return ed;
     if (DIM == 2) return k == 0 ? ed + 4 * kk : kk + 4 * ed;

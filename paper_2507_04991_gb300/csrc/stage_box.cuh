@@ -59,12 +59,12 @@ constexpr unsigned long long kPairSlot2_4 = 0x0e091d1803141f1aull;
 constexpr unsigned long long kPairSlot2_5 = 0x06080a172c110513ull;   // 8 bits per pair
 
 template <int DIM>
-__device__ __forceinline__ int node_slot(int n) {
+__host__ __device__ __forceinline__ int node_slot(int n) {
     if constexpr (DIM == 2) return (int)((kNodeSlot2 >> (4 * n)) & 15u);
     else return n ^ ((n >> 3) & 7);
 }
 template <int DIM>
-__device__ __forceinline__ int pair_slot(int pp) {
+__host__ __device__ __forceinline__ int pair_slot(int pp) {
     if constexpr (DIM == 2) {
         const int w = pp >> 3;
         unsigned long long x = kPairSlot2_0;
@@ -168,7 +168,7 @@ struct NodeTable {
 };
 
 template <int DIM>
-__device__ __forceinline__ void build_node_table(NodeTable<DIM> &T, int q, const float *Df) {
+__host__ __device__ inline void build_node_table(NodeTable<DIM> &T, int q, const float *Df) {
     using B = BoxShape<DIM>;
     constexpr int NP = B::NP, NFP = B::NFP, LPD = B::NPAIR / DIM;
     const int id[3] = {q & 3, (q >> 2) & 3, (q >> 4) & 3};
@@ -276,7 +276,8 @@ __global__ void __launch_bounds__(EPB * ipow4(DIM), box_min_blocks<DIM, EPB, PIP
     const int el = threadIdx.x / NP, q = threadIdx.x % NP, tid = threadIdx.x;
     const size_t NPtot = P.NE * NP;
     const float gm1 = P.gm1_f, inv_gm1 = P.inv_gm1_f, gam = P.gam_f, inv_w = P.inv_w_f;
-    if (el == 0) build_node_table<DIM>(S.tab[q], q, P.Df);
+    // the table is built once on the host (build_node_table) and copied per CTA
+    if (el == 0) S.tab[q] = reinterpret_cast<const NodeTable<DIM> *>(P.box_tab)[q];
     __syncthreads();
     const NodeTable<DIM> &T = S.tab[q];
 

@@ -108,6 +108,7 @@ perrk_status launch_stage(Ctx &c, int stage, bool rhs_only, const double *in_u, 
     P.g_elem_f = c.g_elem_f;
     P.fnorm_f = c.g_fnorm_f;
     P.wJ_f = c.g_wJ_f;
+    P.box_tab = c.g_box_tab;
     P.flags = c.g_flags;
     if (P.n_active <= 0) return PERRK_OK;
     if (c.curved && c.dim != 2) {
@@ -123,6 +124,10 @@ perrk_status launch_stage(Ctx &c, int stage, bool rhs_only, const double *in_u, 
     // mixed form on box elements: kernel variant 0 = the generic stage kernel,
     // 1 = the float4 box kernel, 2 = the box kernel with cp.async staging
     const bool box = mixed && !burgers && !c.curved && c.dim >= 2 && c.stage_variant > 0;
+    if (box && !c.g_box_tab) {
+        set_error("box stage kernel: node table missing");
+        return PERRK_INVALID_ARG;
+    }
     const int epb = c.stage_epb > 0 ? c.stage_epb : default_epb(c.dim);
     const int groups = (P.n_active + epb - 1) / epb;
     int grid = groups;
