@@ -258,11 +258,12 @@ constexpr size_t stage_box_smem_bytes() {
     return sizeof(BoxSmem<DIM, EPB, PIPE>);
 }
 
-// Register budget per thread: 40 in 2D without staging (12 CTAs of 128
-// threads), ~72 with staging, ~96 in 3D.
+// Register budget per thread: 48 in 2D without staging (10 CTAs of 128
+// threads per SM; at 40 the kernel spills, A/B 5% slower per step), ~72 with
+// staging, ~96 in 3D.
 template <int DIM, int EPB, bool PIPE>
 constexpr int box_min_blocks() {
-    return DIM == 2 ? ((PIPE ? 896 : 1536) / (EPB * ipow4(DIM)) > 0 ? (PIPE ? 896 : 1536) / (EPB * ipow4(DIM)) : 1)
+    return DIM == 2 ? ((PIPE ? 896 : 1280) / (EPB * ipow4(DIM)) > 0 ? (PIPE ? 896 : 1280) / (EPB * ipow4(DIM)) : 1)
                     : (EPB * ipow4(DIM) <= 128 ? 640 / (EPB * ipow4(DIM)) : 2);
 }
 
