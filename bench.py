@@ -157,9 +157,9 @@ def reduce_over_ranks(x, world, op):
 # launch (profiles/k_stage_batched2d_traffic.md).  It is reported only while
 # the stage kernel sources are the ones those captures measured.
 STAGE_TRAFFIC = {"workload": "batched2d",
-                 "bytes": {0: 1597560576 + 1228000768,      # generic kernel, 8 elements per CTA
-                           1: 1599218176 + 1246693376},     # box kernel, 16 elements per CTA
-                 "sources_sha256": "083b2471d6da0526e2824d0f748c55b8fcd27cceb93b2d8ed0953002058ef0b8"}
+                 "bytes": {0: 1598393088 + 1228336896,      # generic kernel, 8 elements per CTA
+                           1: 1597633280 + 1228088320},     # box kernel, 8 elements per CTA
+                 "sources_sha256": "9e0bd662bc3ce305c6a8ca5f2c58ab79db039efc060e66606c50b539f1ce77f7"}
 STAGE_SOURCES = ["stage.cuh", "stage_box.cuh", "physics.cuh", "dfloat.cuh", "kernels_stage2d.cu", "stage_launch.cu"]
 
 
@@ -425,7 +425,7 @@ def run_native(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="batched2d")
