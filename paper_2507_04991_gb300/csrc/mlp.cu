@@ -44,7 +44,14 @@ __global__ void k_mlp_guess(const float *__restrict__ W, InstScalars *scal, int 
     if (j == 0) {
         float y = W[ob3];
         for (int k = 0; k < H; ++k) y += red[k];
-        double g0 = S.hist_gamma[0] + (double)W[oOut] * (double)y;
+        // trust region: the learned increment may move the guess from
+        // gamma_{n-1} by at most twice the larger of the last two observed
+        // step-to-step changes (a poorly trained network cannot push Newton,
+        // whose residual test is loose where r(gamma) is flat, to a distant
+        // gamma); no history yet: the method's own guess
+        const double tau = 2.0 * fmax(fabs(S.hist_gamma[0] - S.hist_gamma[1]), fabs(S.hist_gamma[1] - S.hist_gamma[2]));
+        const double inc = fmin(fmax((double)W[oOut] * (double)y, -tau), tau);
+        const double g0 = S.hist_gamma[0] + inc;
         if (isfinite(g0) && fabs(g0 - 1.0) < 0.5) {
             S.gamma = g0;
             S.gamma_guess = g0;
