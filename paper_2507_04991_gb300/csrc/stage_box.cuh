@@ -48,7 +48,7 @@ struct BoxShape {
 // slots below are permutations found by exhaustive local search over the
 // kernel's access pattern (each quarter warp is a row pair of one element):
 // every float4 access of the primitives, states and pair fluxes is then
-// conflict-free.  3D: an XOR swizzle for the nodes, pair fluxes in order.
+// conflict-free.  3D: the permutations below.
 constexpr unsigned long long kNodeSlot2 = 0x71a86c5320f9dbe4ull;   // 4 bits per node
 // pair slots: 8 bits per pair, eight pairs per word
 constexpr unsigned long long kPairSlot2_0 = 0x0c221b2916002d07ull;
@@ -58,14 +58,39 @@ constexpr unsigned long long kPairSlot2_3 = 0x281c0215011e230full;
 constexpr unsigned long long kPairSlot2_4 = 0x0e091d1803141f1aull;
 constexpr unsigned long long kPairSlot2_5 = 0x06080a172c110513ull;   // 8 bits per pair
 
+// 3D: permutations from the same search (quarter-warp conflicts within 2% and
+// 9% of the minimum; an XOR swizzle and the identity were 22% and 52% above)
+constexpr unsigned char kNodeSlot3[64] = {
+    3, 48, 12, 6, 9, 21, 26, 55, 38, 59, 33, 37, 52, 7, 40, 42, 18, 62, 29, 51, 31, 44, 49, 0,
+    24, 58, 47, 36, 13, 46, 35, 57, 61, 23, 41, 50, 14, 32, 19, 20, 4, 53, 22, 17, 43, 34, 15, 8,
+    16, 11, 28, 54, 1, 2, 45, 39, 63, 56, 10, 27, 60, 25, 30, 5,
+};
+constexpr unsigned short kPairSlot3[288] = {
+    114, 275, 205, 176, 249, 7, 206, 252, 208, 101, 278, 259, 119, 233, 66, 284, 231, 160, 157, 59, 228, 178, 134, 73,
+    182, 27, 236, 192, 185, 106, 247, 69, 88, 204, 110, 39, 57, 269, 42, 283, 255, 45, 235, 164, 232, 210, 238, 177,
+    22, 122, 17, 195, 191, 212, 112, 37, 187, 145, 32, 246, 74, 229, 287, 276, 131, 133, 6, 281, 36, 151, 138, 272,
+    211, 128, 223, 50, 60, 214, 189, 65, 10, 87, 261, 115, 188, 262, 40, 81, 44, 41, 250, 5, 179, 48, 95, 190,
+    70, 171, 56, 245, 143, 153, 240, 241, 130, 146, 270, 136, 125, 23, 253, 116, 163, 58, 227, 222, 108, 264, 89, 230,
+    82, 277, 9, 244, 126, 167, 168, 219, 172, 271, 197, 194, 140, 62, 175, 104, 251, 165, 221, 242, 8, 97, 258, 28,
+    19, 256, 201, 20, 279, 54, 285, 34, 76, 193, 24, 135, 266, 102, 237, 67, 86, 68, 96, 103, 11, 149, 18, 137,
+    220, 121, 218, 38, 93, 55, 216, 35, 158, 26, 120, 129, 267, 109, 12, 15, 107, 170, 141, 72, 71, 180, 265, 46,
+    29, 91, 209, 132, 47, 234, 152, 78, 53, 203, 90, 4, 94, 273, 111, 248, 99, 33, 25, 100, 243, 183, 142, 215,
+    84, 169, 254, 162, 184, 173, 263, 75, 156, 30, 213, 43, 154, 127, 64, 49, 260, 16, 51, 31, 282, 117, 1, 166,
+    198, 217, 200, 21, 2, 124, 147, 199, 3, 80, 159, 85, 161, 196, 186, 286, 150, 79, 224, 155, 52, 98, 61, 257,
+    207, 226, 113, 139, 148, 118, 77, 280, 63, 105, 83, 144, 268, 13, 14, 92, 225, 274, 202, 174, 181, 239, 0, 123,
+};
+
+// slot maps, used by the host-side table builder
 template <int DIM>
-__host__ __device__ __forceinline__ int node_slot(int n) {
+inline int node_slot(int n) {
     if constexpr (DIM == 2) return (int)((kNodeSlot2 >> (4 * n)) & 15u);
-    else return n ^ ((n >> 3) & 7);
+    else return kNodeSlot3[n];
 }
 template <int DIM>
-__host__ __device__ __forceinline__ int pair_slot(int pp) {
-    if constexpr (DIM == 2) {
+inline int pair_slot(int pp) {
+    if constexpr (DIM == 3) {
+        return kPairSlot3[pp];
+    } else {
         const int w = pp >> 3;
         unsigned long long x = kPairSlot2_0;
         x = (w == 1) ? kPairSlot2_1 : x;
@@ -75,7 +100,6 @@ __host__ __device__ __forceinline__ int pair_slot(int pp) {
         x = (w == 5) ? kPairSlot2_5 : x;
         return (int)((x >> (8 * (pp & 7))) & 255u);
     }
-    else return pp;
 }
 
 template <int DIM>
@@ -168,7 +192,7 @@ struct NodeTable {
 };
 
 template <int DIM>
-__host__ __device__ inline void build_node_table(NodeTable<DIM> &T, int q, const float *Df) {
+inline void build_node_table(NodeTable<DIM> &T, int q, const float *Df) {   // host
     using B = BoxShape<DIM>;
     constexpr int NP = B::NP, NFP = B::NFP, LPD = B::NPAIR / DIM;
     const int id[3] = {q & 3, (q >> 2) & 3, (q >> 4) & 3};
