@@ -116,7 +116,7 @@ typedef struct {
                                      from K_1, K_{S-1}, K_S; 0: accumulate d at every stage with b_i != 0.
                                      Same sums in the same order either way. */
     int solver;                   /* a perrk_solver value, Newton by default */
-    double bracket_lo, bracket_hi; /* bisection bracket / secant initial guesses (default 0.8, 1.2, Sec. 4.2) */
+    double bracket_lo, bracket_hi; /* bisection bracket / secant initial guesses (default 0.8, 1.2, Sec. 4.3.2) */
 } perrk_options;
 
 /* Per-step record (perrk_step fills one per step when info != NULL). */

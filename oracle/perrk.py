@@ -24,7 +24,7 @@ U_{n+1} = U_n + gamma dt d, t_{n+1} = t_n + gamma dt.
 
 The two other root finders the paper considers (Sec. 3.1), one evaluation of
 r per full-state pass:
-  bisection: r at the bracket ends [lo, hi] (Sec. 4.2 takes [0.8, 1.2]),
+  bisection: r at the bracket ends [lo, hi] (Sec. 4.3.2 takes [0.8, 1.2]),
   which must differ in sign, then at midpoints, keeping the half whose ends
   differ in sign; stop on |r(mid)| <= tol_r A_n or a bracket of length
   <= tol_g (take that midpoint) or after max_it passes;

@@ -415,6 +415,37 @@ EQUATION_CODES = {"burgers1d": BURGERS_1D, "euler1d": EULER_1D, "euler2d": EULER
 SURFACE_CODES = {"ec": SURFACE_EC, "es": SURFACE_ES_RUSANOV, "es_rusanov": SURFACE_ES_RUSANOV}
 
 
+# Root-finder settings the paper uses per test case (Sec. 4): solver, maximum
+# passes, residual tolerance, step (or bracket-length) tolerance and, for
+# bisection, the bracket.  The paper states absolute residual tolerances; here
+# they scale A_n = sum omega J |s(U_n)| (tol_r), which is 1 to O(10) on its
+# cases.  Machine epsilon reads as 2.2e-16.
+_EPS = 2.220446049250313e-16
+NEWTON_PRESETS = {
+    "advection_1d": dict(solver=SOLVER_NEWTON, max_it=10, tol_r=1e-14, tol_g=1e-15),      # Sec. 3.2.1
+    "kelvin_helmholtz": dict(solver=SOLVER_NEWTON, max_it=5, tol_r=1e-15, tol_g=1e-13),   # Sec. 3.2.2
+    "weak_blast": dict(solver=SOLVER_NEWTON, max_it=5, tol_r=_EPS, tol_g=_EPS),           # Sec. 4.1.1
+    "vortex_entropy": dict(solver=SOLVER_NEWTON, max_it=3, tol_r=1e-14, tol_g=1e-15),     # Sec. 4.1.2
+    "vortex_convergence_p2": dict(solver=SOLVER_NEWTON, max_it=5, tol_r=1e-13, tol_g=_EPS),   # Sec. 4.3.1
+    "vortex_convergence_p34": dict(solver=SOLVER_NEWTON, max_it=5, tol_r=1e-14, tol_g=_EPS),
+    "viscous_shock": dict(solver=SOLVER_BISECTION, max_it=25, tol_r=1e-15, tol_g=1e-15,
+                          bracket=(0.8, 1.2)),                                             # Sec. 4.3.2
+    "alfven_wave": dict(solver=SOLVER_NEWTON, max_it=10, tol_r=1e-15, tol_g=1e-15),     # Sec. 4.3.3
+    "sd7003": dict(solver=SOLVER_NEWTON, max_it=5, tol_r=1e-13, tol_g=1e-13),             # Sec. 5.1.2
+    "vrmhd_cylinder": dict(solver=SOLVER_NEWTON, max_it=3, tol_r=1e-14, tol_g=0.0),       # Sec. 5.2.1
+    "naca0012": dict(solver=SOLVER_NEWTON, max_it=5, tol_r=1e-12, tol_g=1e-13),           # Sec. 5.3.1
+    "crm": dict(solver=SOLVER_NEWTON, max_it=5, tol_r=1e-13, tol_g=1e-13),                # Sec. 5.5.1
+}
+
+
+def options_preset(case, **kw):
+    """options() with a test case's root-finder settings from the paper;
+    further keywords override."""
+    args = dict(NEWTON_PRESETS[case])
+    args.update(kw)
+    return options(**args)
+
+
 def options(precision=FP64, relaxation=True, max_it=10, tol_r=1e-14, tol_g=1e-14, guess=GUESS_PREV,
             target=TARGET_DELTA_H, use_graph=False, fuse_direction=True, solver=SOLVER_NEWTON, bracket=(0.8, 1.2)):
     o = perrk_default_options()

@@ -102,3 +102,19 @@ def test_invalid_solver_options_rejected(lib, bad):
     with pytest.raises(pk.PerrkError) as ei:
         pk.perrk_create(m, s, o)
     assert ei.value.status == pk.PERRK_INVALID_ARG
+
+
+@pytest.mark.parametrize("case", sorted(pk.NEWTON_PRESETS))
+def test_newton_presets_accepted(lib, case):
+    """The paper's per-case root-finder settings are valid options (create accepts them)."""
+    wl, keep, m, (c, b, a1, asub) = _small_mesh()
+    s = pk.scheme_desc(3, [6, 3], c, b, a1, asub, pk.EULER_2D, pk.SURFACE_ES_RUSANOV, 1.4, keep)
+    o = pk.options_preset(case)
+    assert o.newton_max_it == pk.NEWTON_PRESETS[case]["max_it"]
+    try:
+        h = pk.perrk_create(m, s, o)
+    except pk.PerrkError as err:
+        # on a machine without a GPU, create stops at the first device allocation
+        assert err.status == pk.PERRK_CUDA_ERROR or err.status == pk.PERRK_OUT_OF_MEMORY
+        return
+    pk.perrk_destroy(h)
