@@ -190,6 +190,28 @@ perrk_status perrk_set_dt(perrk_ctx *ctx, int inst, double dt);
  * nsteps * n_inst records (step-major), which forces a stream sync. */
 perrk_status perrk_step(perrk_ctx *ctx, int nsteps, perrk_step_info *info, void *stream);
 
+/* Relaxation history of one instance: what a resumed run needs besides the
+ * state to continue exactly as an uninterrupted one (the Newton warm start
+ * gamma_{n-1}, Sec. 3.1; H(U_n) as the previous step left it; H(U_0) for
+ * TARGET_INITIAL; the learned-guess history; time and step count). */
+typedef struct {
+    double t;                     /* time */
+    double H_n;                   /* H(U_n) carried from the previous step */
+    double A_n;                   /* sum omega J |s(U_n)| (tolerance scale) */
+    double H0;                    /* H(U_0) */
+    double gamma_hist[3];         /* gamma_{n-1}, gamma_{n-2}, gamma_{n-3} */
+    double dh_hist[3];            /* (Delta H / A) of the last three steps */
+    int64_t steps;                /* steps since the state was set */
+} perrk_resume_info;
+
+/* Checkpoint: copy the history of every instance into out[n_inst] (host);
+ * syncs.  Resume: after perrk_set_state with the checkpointed state, overwrite
+ * the history set_state initialised with in[n_inst]; syncs.  Together with
+ * perrk_get_state this makes a resumed run bit-identical to an uninterrupted
+ * one. */
+perrk_status perrk_get_resume(const perrk_ctx *ctx, perrk_resume_info *out, void *stream);
+perrk_status perrk_set_resume(perrk_ctx *ctx, const perrk_resume_info *in, void *stream);
+
 /* Autotune the launch mapping of ctx on the current device: times the first
  * and the last stage kernel for every valid elements-per-CTA choice, grid
  * mapping (one CTA per element group, or a persistent grid of k CTAs per SM)

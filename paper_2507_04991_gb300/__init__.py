@@ -33,7 +33,8 @@ EXPORTED = [
     "perrk_default_options", "perrk_create", "perrk_create_batched", "perrk_destroy", "perrk_build_tableau",
     "perrk_shape", "perrk_set_state", "perrk_get_state", "perrk_set_dt", "perrk_step", "perrk_entropy",
     "perrk_rhs", "perrk_mlp_size", "perrk_mlp_features", "perrk_set_mlp", "perrk_mlp_train", "perrk_mlp_grad",
-    "perrk_last_error", "perrk_status_string", "perrk_launch_stage", "perrk_stage_info", "perrk_df_log", "perrk_autotune", "perrk_tuning", "perrk_set_tuning", "perrk_entropy_static",
+    "perrk_last_error", "perrk_status_string", "perrk_launch_stage", "perrk_stage_info", "perrk_df_log", "perrk_autotune", "perrk_tuning", "perrk_set_tuning", "perrk_entropy_static", "perrk_get_resume",
+    "perrk_set_resume",
 ]
 
 
@@ -103,6 +104,8 @@ def load(path=LIB_PATH):
         "perrk_autotune": (I, [P, P, P]),
         "perrk_tuning": (I, [P, P, P, P, P]),
         "perrk_set_tuning": (I, [P, I, I, I, I]),
+        "perrk_get_resume": (I, [P, P, P]),
+        "perrk_set_resume": (I, [P, P, P]),
         "perrk_entropy_static": (I, [I, D, P, P, C.c_longlong, P, P]),
         "perrk_stage_info": (I, [P, I, P, P, P, P, P]),
         "perrk_status_string": (C.c_char_p, [I]),
@@ -300,6 +303,24 @@ def perrk_autotune(h, stream=0):
     ms = C.c_float(0.0)
     _check(load().perrk_autotune(h, C.c_void_p(stream), C.byref(ms)), "perrk_autotune")
     return ms.value
+
+
+class perrk_resume_info(C.Structure):
+    _fields_ = [("t", C.c_double), ("H_n", C.c_double), ("A_n", C.c_double), ("H0", C.c_double),
+                ("gamma_hist", C.c_double * 3), ("dh_hist", C.c_double * 3), ("steps", C.c_int64)]
+
+
+def perrk_get_resume(h, stream=0):
+    """Relaxation history of every instance (checkpoint, with perrk_get_state)."""
+    n_inst = perrk_shape(h)[3]
+    arr = (perrk_resume_info * n_inst)()
+    _check(load().perrk_get_resume(h, arr, C.c_void_p(stream)), "perrk_get_resume")
+    return arr
+
+
+def perrk_set_resume(h, arr, stream=0):
+    """Restore the history from perrk_get_resume after perrk_set_state."""
+    _check(load().perrk_set_resume(h, arr, C.c_void_p(stream)), "perrk_set_resume")
 
 
 def perrk_set_tuning(h, elems_per_cta, persistent_grid=0, relax_threads=128, stage_variant=1):
@@ -517,3 +538,13 @@ class Solver:
 
     def set_mlp(self, w):
         perrk_set_mlp(self.h, w)
+
+    def checkpoint(self):
+        """(state, relaxation history): all a resumed run needs to continue
+        bit-identically (options, tableaux, dt and guess weights aside)."""
+        return self.state(), perrk_get_resume(self.h)
+
+    def resume(self, ckpt):
+        u, hist = ckpt
+        self.set_state(u)
+        perrk_set_resume(self.h, hist)

@@ -277,6 +277,62 @@ perrk_status perrk_get_state(perrk_ctx *h, double *u, int on_device, void *strea
     return PERRK_OK;
 }
 
+perrk_status perrk_get_resume(const perrk_ctx *h, perrk_resume_info *out, void *stream) {
+    if (!h || !out) return PERRK_INVALID_ARG;
+    const Ctx &c = h->c;
+    std::vector<InstScalars> sc(c.n_inst);
+    cudaStream_t st = (cudaStream_t)stream;
+    PERRK_CUDA(cudaMemcpyAsync(sc.data(), c.g_scal, sc.size() * sizeof(InstScalars), cudaMemcpyDeviceToHost, st),
+               "resume copy");
+    PERRK_CUDA(cudaStreamSynchronize(st), "resume sync");
+    for (int k = 0; k < c.n_inst; ++k) {
+        perrk_resume_info &r = out[k];
+        r.t = sc[k].t;
+        r.H_n = sc[k].H_n;
+        r.A_n = sc[k].A_n;
+        r.H0 = sc[k].H0;
+        for (int j = 0; j < 3; ++j) {
+            r.gamma_hist[j] = sc[k].hist_gamma[j];
+            r.dh_hist[j] = sc[k].hist_dh[j];
+        }
+        r.steps = sc[k].nsteps_done;
+    }
+    return PERRK_OK;
+}
+
+perrk_status perrk_set_resume(perrk_ctx *h, const perrk_resume_info *in, void *stream) {
+    if (!h || !in) return PERRK_INVALID_ARG;
+    Ctx &c = h->c;
+    for (int k = 0; k < c.n_inst; ++k)
+        if (!std::isfinite(in[k].t) || !std::isfinite(in[k].H_n) || in[k].steps < 0 || in[k].steps != in[0].steps) {
+            set_error("set_resume: non-finite history or instances at different step counts");
+            return PERRK_INVALID_ARG;
+        }
+    std::vector<InstScalars> sc(c.n_inst);
+    cudaStream_t st = (cudaStream_t)stream;
+    PERRK_CUDA(cudaMemcpyAsync(sc.data(), c.g_scal, sc.size() * sizeof(InstScalars), cudaMemcpyDeviceToHost, st),
+               "resume copy");
+    PERRK_CUDA(cudaStreamSynchronize(st), "resume sync");
+    for (int k = 0; k < c.n_inst; ++k) {
+        const perrk_resume_info &r = in[k];
+        sc[k].t = r.t;
+        sc[k].H_n = r.H_n;
+        sc[k].A_n = r.A_n;
+        sc[k].H0 = r.H0;
+        for (int j = 0; j < 3; ++j) {
+            sc[k].hist_gamma[j] = r.gamma_hist[j];
+            sc[k].hist_dh[j] = r.dh_hist[j];
+        }
+        sc[k].gamma = r.gamma_hist[0];
+        sc[k].nsteps_done = (int32_t)r.steps;
+    }
+    PERRK_CUDA(cudaMemcpyAsync(c.g_scal, sc.data(), sc.size() * sizeof(InstScalars), cudaMemcpyHostToDevice, st),
+               "resume upload");
+    PERRK_CUDA(cudaStreamSynchronize(st), "resume sync");
+    h->host_steps = in[0].steps;
+    return PERRK_OK;
+}
+
 perrk_status perrk_set_dt(perrk_ctx *h, int inst, double dt) {
     if (!h || !(dt > 0.0) || !std::isfinite(dt) || inst < -1 || inst >= h->c.n_inst) {
         set_error("bad instance or dt");
