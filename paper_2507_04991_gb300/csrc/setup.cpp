@@ -499,13 +499,23 @@ void df_tables(double gamma_gas, std::vector<float> &tab, std::vector<float> &co
 extern "C" perrk_status perrk_build_tableau(int p, int R, const int32_t *E, int S_cap, int *S_out, double *c, double *b,
                                            double *a1, double *asub) {
     using namespace perrk;
-    if (p < 2 || p > 4 || R < 1 || R > kMaxR || !E || !S_out || !c || !b || !a1 || !asub) return PERRK_INVALID_ARG;
+    if (p < 2 || p > 4 || R < 1 || R > kMaxR || !E || !S_out || !c || !b || !a1 || !asub) {
+        set_error("build_tableau: p must be 2..4, R 1.." + std::to_string(kMaxR) + ", pointers non-null");
+        return PERRK_INVALID_ARG;
+    }
     int S = 0;
     for (int r = 0; r < R; ++r) {
-        if (E[r] < min_E(p)) return PERRK_INVALID_ARG;
+        if (E[r] < min_E(p)) {
+            set_error("build_tableau: E[" + std::to_string(r) + "] = " + std::to_string(E[r]) +
+                      " is below the archetype minimum " + std::to_string(min_E(p)));
+            return PERRK_INVALID_ARG;
+        }
         S = std::max(S, (int)E[r]);
     }
-    if (S > S_cap || S > 64) return PERRK_INVALID_ARG;
+    if (S > S_cap || S > 64) {
+        set_error("build_tableau: S = " + std::to_string(S) + " exceeds the output capacity or 64");
+        return PERRK_INVALID_ARG;
+    }
     *S_out = S;
     // shared abscissae and weights (1-based stage i -> index i-1)
     std::vector<double> cc(S + 1, 0.0);

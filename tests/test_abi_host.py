@@ -86,6 +86,13 @@ def test_invalid_input_rejected(lib, breakage):
     assert pk.last_error()
 
 
+def test_tableau_below_archetype_minimum_rejected(lib):
+    with pytest.raises(pk.PerrkError) as ei:
+        pk.perrk_build_tableau(3, [6, 4, 2])
+    assert ei.value.status == pk.PERRK_INVALID_ARG
+    assert "archetype minimum" in pk.last_error()
+
+
 def test_status_strings(lib):
     assert pk.status_string(0) == "ok"
     assert pk.status_string(3) == "non-physical state"
