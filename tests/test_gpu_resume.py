@@ -21,7 +21,7 @@ def _built():
 
 def _problems():
     return [workloads.small_box_2d(n=6, seed=31, R=3, E=[7, 5, 3], order=3, random_parts=True),
-            workloads.small_box_2d(n=6, seed=32, R=2, E=[4, 2], order=3)]
+            workloads.small_box_2d(n=6, seed=32, R=2, E=[4, 3], order=3)]
 
 
 def _fields(recs):
