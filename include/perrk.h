@@ -190,12 +190,32 @@ perrk_status perrk_set_dt(perrk_ctx *ctx, int inst, double dt);
  * nsteps * n_inst records (step-major), which forces a stream sync. */
 perrk_status perrk_step(perrk_ctx *ctx, int nsteps, perrk_step_info *info, void *stream);
 
-/* Relaxation history of one instance: what a resumed run needs besides the
- * state to continue exactly as an uninterrupted one (the Newton warm start
- * gamma_{n-1}, Sec. 3.1; H(U_n) as the previous step left it; H(U_0) for
- * TARGET_INITIAL; the learned-guess history; time and step count). */
+/* Checkpoint / resume.  A checkpoint is a host byte buffer holding everything
+ * a resumed run needs to continue bit-identically to an uninterrupted one:
+ *
+ *   perrk_checkpoint_header
+ *   perrk_resume_info[n_inst]     the relaxation history of each instance
+ *   the state in the context's own representation: float64 [V][n_elem][NP]
+ *   (float64 form) or the float pair hi[V][n_elem][NP] then lo[...] (mixed
+ *   form; a float64 round trip through perrk_get_state would round lo).
+ *
+ * The history carries the Newton warm start gamma_{n-1} (Sec. 3.1), H(U_n)
+ * as the previous step left it, the tolerance scale A_n, H(U_0) for
+ * TARGET_INITIAL, the learned-guess history, dt, time and step count.  The
+ * mesh, tableaux, options and guess weights are the caller's: load a
+ * checkpoint into a context created with the same inputs. */
+typedef struct {
+    uint32_t magic;               /* PERRK_CHECKPOINT_MAGIC */
+    uint32_t version;             /* 1 */
+    int32_t precision, n_inst, n_elem, nvar, np, reserved;
+    uint64_t state_bytes;         /* bytes of the state section */
+} perrk_checkpoint_header;
+
+#define PERRK_CHECKPOINT_MAGIC 0x4b435250u   /* "PRCK" */
+
 typedef struct {
     double t;                     /* time */
+    double dt;                    /* step size of the instance */
     double H_n;                   /* H(U_n) carried from the previous step */
     double A_n;                   /* sum omega J |s(U_n)| (tolerance scale) */
     double H0;                    /* H(U_0) */
@@ -204,13 +224,15 @@ typedef struct {
     int64_t steps;                /* steps since the state was set */
 } perrk_resume_info;
 
-/* Checkpoint: copy the history of every instance into out[n_inst] (host);
- * syncs.  Resume: after perrk_set_state with the checkpointed state, overwrite
- * the history set_state initialised with in[n_inst]; syncs.  Together with
- * perrk_get_state this makes a resumed run bit-identical to an uninterrupted
- * one. */
-perrk_status perrk_get_resume(const perrk_ctx *ctx, perrk_resume_info *out, void *stream);
-perrk_status perrk_set_resume(perrk_ctx *ctx, const perrk_resume_info *in, void *stream);
+/* Size in bytes of a checkpoint of this context (0 for a null context). */
+size_t perrk_checkpoint_size(const perrk_ctx *ctx);
+/* Write a checkpoint into buf (host, at least perrk_checkpoint_size bytes);
+ * syncs the stream.  INVALID_ARG if buf is null or too small. */
+perrk_status perrk_checkpoint_save(perrk_ctx *ctx, void *buf, size_t size, void *stream);
+/* Restore state and history from a checkpoint; syncs.  INVALID_ARG if the
+ * header does not match this context (precision, shapes) or the buffer is
+ * short; the context is unchanged then. */
+perrk_status perrk_checkpoint_load(perrk_ctx *ctx, const void *buf, size_t size, void *stream);
 
 /* Autotune the launch mapping of ctx on the current device: times the first
  * and the last stage kernel for every valid elements-per-CTA choice, grid

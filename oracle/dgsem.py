@@ -122,4 +122,89 @@ def rhs(geo, phys, U):
         accm = np.moveaxis(acc, ax, -1)                # view
         np.add.at(accm[..., N], (slice(None), el), cL)
         np.add.at(accm[..., 0], (slice(None), er), cR)
-    return -geo.flat(acc) / geo.J[None]
+    K = -geo.flat(acc) / geo.J[None]
+    if getattr(phys, "viscous", False):
+        K = K + viscous_rhs(geo, phys, U)
+    return K
+
+
+# ----------------------------------------------------------------------------
+# Parabolic part: BR1 (Bassi & Rebay 1997; Gassner, Winters, Hindenlang &
+# Kopriva 2018), the viscous discretisation of the paper's viscous test
+# (Sec. 4.2), with the gradients taken of the entropy variables.
+#
+# Gradient (one element, strong form, central trace W* = (W^- + W^+)/2):
+#   J_q q_l(q) = sum_k Ja^k_l(q) sum_m D_{qm} W(m along xi^k)
+#                + sum_{faces at q} (1/omega_face) (W* - W_q) nu_l
+# Divergence of the viscous flux (central flux f_v* = (f_v^- + f_v^+)/2):
+#   J_q (div f_v)_q = sum_k sum_m D_{qm} (sum_l Ja^k_l f_v,l)(m along xi^k)
+#                + sum_{faces at q} (1/omega_face) (f_v* - f_v(q)) . nu
+# with nu the element's outward scaled normal; the viscous contribution to
+# the right-hand side is + div f_v.  Both face terms use the '+' side's
+# normal for the two elements of an interface, like the inviscid part.
+# ----------------------------------------------------------------------------
+
+def _interfaces(geo, k):
+    eL, fL, eR = geo.faces[:, 0], geo.faces[:, 1], geo.faces[:, 2]
+    sel = fL == 2 * k + 1
+    return eL[sel], eR[sel]
+
+
+def br1_gradient(geo, W):
+    """q[l, V, n_elem, NP] ~ d W / d x_l for a nodal field W[V, n_elem, NP]."""
+    d, N = geo.dim, geo.N
+    Wt = geo.tens(W)
+    JQ = np.zeros((d,) + Wt.shape)
+    for k in range(d):
+        dW = geo.tens(geo.dxi(W, k))
+        Jak = geo.tens(geo.Ja[k])
+        for l in range(d):
+            JQ[l] += Jak[l][None] * dW
+    for k in range(d):
+        el, er = _interfaces(geo, k)
+        if el.size == 0:
+            continue
+        ax = Wt.ndim - 1 - k
+        Wk = np.moveaxis(Wt, ax, -1)
+        wL, wR = Wk[..., N][:, el], Wk[..., 0][:, er]
+        nu = np.moveaxis(geo.tens(geo.Ja[k]), ax, -1)[..., N][:, el]
+        half = 0.5 * (wR - wL)          # W* - W_L;  W* - W_R = -half
+        for l in range(d):
+            Ql = np.moveaxis(JQ[l], ax, -1)
+            # left element, outward normal +nu;  right element, outward -nu
+            np.add.at(Ql[..., N], (slice(None), el), half * nu[l][None] / geo.w[N])
+            np.add.at(Ql[..., 0], (slice(None), er), (-half) * (-nu[l][None]) / geo.w[0])
+    return geo.flat(JQ) / geo.J[None, None]
+
+
+def br1_divergence(geo, Fv):
+    """(div f_v)[V, n_elem, NP] for a nodal flux Fv[l, V, n_elem, NP]."""
+    d, N = geo.dim, geo.N
+    acc = np.zeros(geo.tens(Fv[0]).shape)
+    for k in range(d):
+        Fk = sum(geo.Ja[k][l][None] * Fv[l] for l in range(d))    # contravariant component k
+        acc += geo.tens(geo.dxi(Fk, k))
+    for k in range(d):
+        el, er = _interfaces(geo, k)
+        if el.size == 0:
+            continue
+        ax = acc.ndim - 1 - k
+        nu = np.moveaxis(geo.tens(geo.Ja[k]), ax, -1)[..., N][:, el]
+        fnL = 0.0
+        fnR = 0.0
+        for l in range(d):
+            Fl = np.moveaxis(geo.tens(Fv[l]), ax, -1)
+            fnL = fnL + Fl[..., N][:, el] * nu[l][None]
+            fnR = fnR + Fl[..., 0][:, er] * nu[l][None]
+        half = 0.5 * (fnR - fnL)
+        accm = np.moveaxis(acc, ax, -1)
+        # left: (f* - f_L) . nu = half;  right: (f* - f_R) . (-nu) = half
+        np.add.at(accm[..., N], (slice(None), el), half / geo.w[N])
+        np.add.at(accm[..., 0], (slice(None), er), half / geo.w[0])
+    return geo.flat(acc) / geo.J[None]
+
+
+def viscous_rhs(geo, phys, U):
+    """+ div f_v(U, grad w) with the BR1 gradient of the entropy variables."""
+    Q = br1_gradient(geo, phys.entropy_vars(U))
+    return br1_divergence(geo, phys.viscous_flux(U, Q))

@@ -73,7 +73,8 @@ class StepRecord:
 class Solver:
     def __init__(self, wl, opts=None, p=None, E=None):
         self.wl = wl
-        self.phys = physics.Physics(wl.equation, wl.surface_flux, wl.gamma_gas)
+        self.phys = physics.Physics(wl.equation, wl.surface_flux, wl.gamma_gas, getattr(wl, "mu", 0.0),
+                                    getattr(wl, "prandtl", 0.75))
         self.geo = dgsem.Geometry(wl.coords, wl.faces)
         self.p = p or wl.order
         self.E = list(E or wl.E)

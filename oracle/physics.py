@@ -131,15 +131,50 @@ def euler_entropy_potential(u, n, gamma):
     return (gamma - 1.0) * rho * np.sum(v * n, axis=0)
 
 
+# ------------------------------------------------- Navier-Stokes-Fourier ---
+
+def nsf_viscous_flux(u, gw, gamma, mu, prandtl):
+    """Viscous flux of the compressible Navier-Stokes-Fourier equations (the
+    parabolic part of the paper's viscous test, Sec. 4.2: constant dynamic
+    viscosity mu, Stokes' hypothesis, Fourier heat conduction with Prandtl
+    number Pr = c_p mu / kappa, c_p = gamma / (gamma - 1), gas constant 1 so
+    T = p / rho).
+
+    The gradients come as gw[l] = d w / d x_l of the entropy variables of the
+    paper's entropy (eq. EntropyVariables).  With w_m = (gamma-1) v / T and
+    w_E = -(gamma-1) / T the primitive gradients follow by the chain rule:
+        d T = (gamma-1) d w_E / w_E^2,      d v = -(d w_m + v d w_E) / w_E.
+    Stress tau = mu (grad v + grad v^T) - 2/3 mu (div v) I, heat flux
+    -kappa grad T.  Returns fv[l] = (0, tau[l, :], tau[l, :] . v + kappa d_l T)."""
+    dim = u.shape[0] - 2
+    rho, v, p = euler_prims(u, gamma)
+    T = p / rho
+    wE = -(gamma - 1.0) / T
+    dT = np.array([(gamma - 1.0) * gw[l][-1] / (wE * wE) for l in range(dim)])
+    dv = np.array([[-(gw[l][1 + a] + v[a] * gw[l][-1]) / wE for a in range(dim)] for l in range(dim)])  # dv[l][a] = d v_a / d x_l
+    div = sum(dv[a][a] for a in range(dim))
+    kappa = mu * gamma / ((gamma - 1.0) * prandtl)
+    fv = np.zeros((dim,) + u.shape)
+    for l in range(dim):
+        for a in range(dim):
+            tau = mu * (dv[l][a] + dv[a][l]) - (2.0 / 3.0) * mu * div * (1.0 if a == l else 0.0)
+            fv[l][1 + a] = tau
+            fv[l][-1] += tau * v[a]
+        fv[l][-1] += kappa * dT[l]
+    return fv
+
+
 # ------------------------------------------------------------- dispatch ---
 
 class Physics:
     """Bundle of the functions one equation needs."""
 
-    def __init__(self, equation, surface="ec", gamma=1.4):
+    def __init__(self, equation, surface="ec", gamma=1.4, mu=0.0, prandtl=0.75):
         self.equation = equation
         self.gamma = gamma
         self.surface = surface
+        self.mu = mu
+        self.prandtl = prandtl
         if equation == "burgers1d":
             self.dim, self.nvar = 1, 1
         else:
@@ -172,3 +207,10 @@ class Physics:
         if self.equation == "burgers1d":
             return burgers_entropy_vars(u)
         return euler_entropy_vars(u, self.gamma)
+
+    @property
+    def viscous(self):
+        return self.mu > 0.0 and self.equation != "burgers1d"
+
+    def viscous_flux(self, u, gw):
+        return nsf_viscous_flux(u, gw, self.gamma, self.mu, self.prandtl)

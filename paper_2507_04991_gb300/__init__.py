@@ -33,8 +33,8 @@ EXPORTED = [
     "perrk_default_options", "perrk_create", "perrk_create_batched", "perrk_destroy", "perrk_build_tableau",
     "perrk_shape", "perrk_set_state", "perrk_get_state", "perrk_set_dt", "perrk_step", "perrk_entropy",
     "perrk_rhs", "perrk_mlp_size", "perrk_mlp_features", "perrk_set_mlp", "perrk_mlp_train", "perrk_mlp_grad",
-    "perrk_last_error", "perrk_status_string", "perrk_launch_stage", "perrk_stage_info", "perrk_df_log", "perrk_autotune", "perrk_tuning", "perrk_set_tuning", "perrk_entropy_static", "perrk_get_resume",
-    "perrk_set_resume",
+    "perrk_last_error", "perrk_status_string", "perrk_launch_stage", "perrk_stage_info", "perrk_df_log", "perrk_autotune", "perrk_tuning", "perrk_set_tuning", "perrk_entropy_static", "perrk_checkpoint_size",
+    "perrk_checkpoint_save", "perrk_checkpoint_load",
 ]
 
 
@@ -104,8 +104,9 @@ def load(path=LIB_PATH):
         "perrk_autotune": (I, [P, P, P]),
         "perrk_tuning": (I, [P, P, P, P, P]),
         "perrk_set_tuning": (I, [P, I, I, I, I]),
-        "perrk_get_resume": (I, [P, P, P]),
-        "perrk_set_resume": (I, [P, P, P]),
+        "perrk_checkpoint_size": (C.c_size_t, [P]),
+        "perrk_checkpoint_save": (I, [P, P, C.c_size_t, P]),
+        "perrk_checkpoint_load": (I, [P, P, C.c_size_t, P]),
         "perrk_entropy_static": (I, [I, D, P, P, C.c_longlong, P, P]),
         "perrk_stage_info": (I, [P, I, P, P, P, P, P]),
         "perrk_status_string": (C.c_char_p, [I]),
@@ -305,22 +306,40 @@ def perrk_autotune(h, stream=0):
     return ms.value
 
 
+class perrk_checkpoint_header(C.Structure):
+    _fields_ = [("magic", C.c_uint32), ("version", C.c_uint32), ("precision", C.c_int32), ("n_inst", C.c_int32),
+                ("n_elem", C.c_int32), ("nvar", C.c_int32), ("np", C.c_int32), ("reserved", C.c_int32),
+                ("state_bytes", C.c_uint64)]
+
+
 class perrk_resume_info(C.Structure):
-    _fields_ = [("t", C.c_double), ("H_n", C.c_double), ("A_n", C.c_double), ("H0", C.c_double),
+    _fields_ = [("t", C.c_double), ("dt", C.c_double), ("H_n", C.c_double), ("A_n", C.c_double), ("H0", C.c_double),
                 ("gamma_hist", C.c_double * 3), ("dh_hist", C.c_double * 3), ("steps", C.c_int64)]
 
 
-def perrk_get_resume(h, stream=0):
-    """Relaxation history of every instance (checkpoint, with perrk_get_state)."""
-    n_inst = perrk_shape(h)[3]
-    arr = (perrk_resume_info * n_inst)()
-    _check(load().perrk_get_resume(h, arr, C.c_void_p(stream)), "perrk_get_resume")
-    return arr
+def perrk_checkpoint_size(h):
+    return int(load().perrk_checkpoint_size(h))
 
 
-def perrk_set_resume(h, arr, stream=0):
-    """Restore the history from perrk_get_resume after perrk_set_state."""
-    _check(load().perrk_set_resume(h, arr, C.c_void_p(stream)), "perrk_set_resume")
+def perrk_checkpoint_save(h, stream=0):
+    """Checkpoint as bytes: header, per-instance relaxation history, state."""
+    n = perrk_checkpoint_size(h)
+    buf = C.create_string_buffer(n)
+    _check(load().perrk_checkpoint_save(h, buf, n, C.c_void_p(stream)), "perrk_checkpoint_save")
+    return buf.raw
+
+
+def perrk_checkpoint_load(h, data, stream=0):
+    buf = C.create_string_buffer(bytes(data), len(data))
+    _check(load().perrk_checkpoint_load(h, buf, len(data), C.c_void_p(stream)), "perrk_checkpoint_load")
+
+
+def checkpoint_history(data):
+    """(header, [perrk_resume_info per instance]) parsed from checkpoint bytes."""
+    hd = perrk_checkpoint_header.from_buffer_copy(data[:C.sizeof(perrk_checkpoint_header)])
+    off = C.sizeof(perrk_checkpoint_header)
+    sz = C.sizeof(perrk_resume_info)
+    return hd, [perrk_resume_info.from_buffer_copy(data[off + k * sz:off + (k + 1) * sz]) for k in range(hd.n_inst)]
 
 
 def perrk_set_tuning(h, elems_per_cta, persistent_grid=0, relax_threads=128, stage_variant=1):
@@ -540,11 +559,9 @@ class Solver:
         perrk_set_mlp(self.h, w)
 
     def checkpoint(self):
-        """(state, relaxation history): all a resumed run needs to continue
-        bit-identically (options, tableaux, dt and guess weights aside)."""
-        return self.state(), perrk_get_resume(self.h)
+        """Checkpoint bytes (state in the context's own representation and the
+        relaxation history): a resumed run continues bit-identically."""
+        return perrk_checkpoint_save(self.h)
 
-    def resume(self, ckpt):
-        u, hist = ckpt
-        self.set_state(u)
-        perrk_set_resume(self.h, hist)
+    def resume(self, data):
+        perrk_checkpoint_load(self.h, data)

@@ -277,17 +277,52 @@ perrk_status perrk_get_state(perrk_ctx *h, double *u, int on_device, void *strea
     return PERRK_OK;
 }
 
-perrk_status perrk_get_resume(const perrk_ctx *h, perrk_resume_info *out, void *stream) {
-    if (!h || !out) return PERRK_INVALID_ARG;
+static size_t state_section_bytes(const Ctx &c) {
+    const size_t n = (size_t)c.V * c.n_elem * c.NP;
+    return c.Uf ? 2 * n * sizeof(float) : n * sizeof(double);
+}
+
+size_t perrk_checkpoint_size(const perrk_ctx *h) {
+    if (!h) return 0;
+    return sizeof(perrk_checkpoint_header) + (size_t)h->c.n_inst * sizeof(perrk_resume_info) +
+           state_section_bytes(h->c);
+}
+
+perrk_status perrk_checkpoint_save(perrk_ctx *h, void *buf, size_t size, void *stream) {
+    if (!h || !buf || size < perrk_checkpoint_size(h)) {
+        set_error("checkpoint_save: null context or buffer, or buffer smaller than perrk_checkpoint_size");
+        return PERRK_INVALID_ARG;
+    }
     const Ctx &c = h->c;
-    std::vector<InstScalars> sc(c.n_inst);
     cudaStream_t st = (cudaStream_t)stream;
+    unsigned char *out = static_cast<unsigned char *>(buf);
+    perrk_checkpoint_header hd{};
+    hd.magic = PERRK_CHECKPOINT_MAGIC;
+    hd.version = 1;
+    hd.precision = c.opt.precision;
+    hd.n_inst = c.n_inst;
+    hd.n_elem = c.n_elem;
+    hd.nvar = c.V;
+    hd.np = c.NP;
+    hd.state_bytes = state_section_bytes(c);
+    std::vector<InstScalars> sc(c.n_inst);
     PERRK_CUDA(cudaMemcpyAsync(sc.data(), c.g_scal, sc.size() * sizeof(InstScalars), cudaMemcpyDeviceToHost, st),
-               "resume copy");
-    PERRK_CUDA(cudaStreamSynchronize(st), "resume sync");
+               "checkpoint scalars");
+    unsigned char *state = out + sizeof hd + (size_t)c.n_inst * sizeof(perrk_resume_info);
+    const size_t n = (size_t)c.V * c.n_elem * c.NP;
+    if (c.Uf) {
+        PERRK_CUDA(cudaMemcpyAsync(state, c.Uf, n * sizeof(float), cudaMemcpyDeviceToHost, st), "checkpoint state");
+        PERRK_CUDA(cudaMemcpyAsync(state + n * sizeof(float), c.Ul, n * sizeof(float), cudaMemcpyDeviceToHost, st),
+                   "checkpoint state");
+    } else {
+        PERRK_CUDA(cudaMemcpyAsync(state, c.U, n * sizeof(double), cudaMemcpyDeviceToHost, st), "checkpoint state");
+    }
+    PERRK_CUDA(cudaStreamSynchronize(st), "checkpoint sync");
+    memcpy(out, &hd, sizeof hd);
     for (int k = 0; k < c.n_inst; ++k) {
-        perrk_resume_info &r = out[k];
+        perrk_resume_info r{};
         r.t = sc[k].t;
+        r.dt = c.inst[k].dt;
         r.H_n = sc[k].H_n;
         r.A_n = sc[k].A_n;
         r.H0 = sc[k].H0;
@@ -296,26 +331,63 @@ perrk_status perrk_get_resume(const perrk_ctx *h, perrk_resume_info *out, void *
             r.dh_hist[j] = sc[k].hist_dh[j];
         }
         r.steps = sc[k].nsteps_done;
+        memcpy(out + sizeof hd + (size_t)k * sizeof r, &r, sizeof r);
     }
     return PERRK_OK;
 }
 
-perrk_status perrk_set_resume(perrk_ctx *h, const perrk_resume_info *in, void *stream) {
-    if (!h || !in) return PERRK_INVALID_ARG;
+perrk_status perrk_checkpoint_load(perrk_ctx *h, const void *buf, size_t size, void *stream) {
+    if (!h || !buf || size < sizeof(perrk_checkpoint_header)) {
+        set_error("checkpoint_load: null context or buffer, or buffer shorter than the header");
+        return PERRK_INVALID_ARG;
+    }
     Ctx &c = h->c;
+    const unsigned char *in = static_cast<const unsigned char *>(buf);
+    perrk_checkpoint_header hd;
+    memcpy(&hd, in, sizeof hd);
+    if (hd.magic != PERRK_CHECKPOINT_MAGIC || hd.version != 1 || hd.precision != c.opt.precision ||
+        hd.n_inst != c.n_inst || hd.n_elem != c.n_elem || hd.nvar != c.V || hd.np != c.NP ||
+        hd.state_bytes != state_section_bytes(c) || size < perrk_checkpoint_size(h)) {
+        set_error("checkpoint_load: the checkpoint does not match this context (format, precision or shapes)");
+        return PERRK_INVALID_ARG;
+    }
+    std::vector<perrk_resume_info> rs(c.n_inst);
+    memcpy(rs.data(), in + sizeof hd, rs.size() * sizeof(perrk_resume_info));
     for (int k = 0; k < c.n_inst; ++k)
-        if (!std::isfinite(in[k].t) || !std::isfinite(in[k].H_n) || in[k].steps < 0 || in[k].steps != in[0].steps) {
-            set_error("set_resume: non-finite history or instances at different step counts");
+        if (!std::isfinite(rs[k].t) || !std::isfinite(rs[k].H_n) || !(rs[k].dt > 0.0) || !std::isfinite(rs[k].dt) ||
+            rs[k].steps < 0 || rs[k].steps != rs[0].steps) {
+            set_error("checkpoint_load: non-finite history, bad dt, or instances at different step counts");
             return PERRK_INVALID_ARG;
         }
-    std::vector<InstScalars> sc(c.n_inst);
     cudaStream_t st = (cudaStream_t)stream;
+    PERRK_CUDA(cudaStreamSynchronize(st), "checkpoint sync");
+    bool dt_changed = false;
+    for (int k = 0; k < c.n_inst; ++k)
+        if (c.inst[k].dt != rs[k].dt) {
+            c.inst[k].dt = rs[k].dt;
+            dt_changed = true;
+        }
+    if (dt_changed) PERRK_TRY(upload_coefficients(c));
+    const unsigned char *state = in + sizeof hd + rs.size() * sizeof(perrk_resume_info);
+    const size_t n = (size_t)c.V * c.n_elem * c.NP;
+    if (c.Uf) {
+        PERRK_CUDA(cudaMemcpyAsync(c.Uf, state, n * sizeof(float), cudaMemcpyHostToDevice, st), "checkpoint state");
+        PERRK_CUDA(cudaMemcpyAsync(c.Ul, state + n * sizeof(float), n * sizeof(float), cudaMemcpyHostToDevice, st),
+                   "checkpoint state");
+    } else {
+        PERRK_CUDA(cudaMemcpyAsync(c.U, state, n * sizeof(double), cudaMemcpyHostToDevice, st), "checkpoint state");
+    }
+    PERRK_CUDA(cudaMemsetAsync(c.g_flags, 0, sizeof(uint32_t), st), "flags clear");
+    // the per-step scalars start from what set_state leaves, then take the history
+    PERRK_TRY(launch_entropy_set(c, st));
+    std::vector<InstScalars> sc(c.n_inst);
     PERRK_CUDA(cudaMemcpyAsync(sc.data(), c.g_scal, sc.size() * sizeof(InstScalars), cudaMemcpyDeviceToHost, st),
-               "resume copy");
-    PERRK_CUDA(cudaStreamSynchronize(st), "resume sync");
+               "checkpoint scalars");
+    PERRK_CUDA(cudaStreamSynchronize(st), "checkpoint sync");
     for (int k = 0; k < c.n_inst; ++k) {
-        const perrk_resume_info &r = in[k];
+        const perrk_resume_info &r = rs[k];
         sc[k].t = r.t;
+        sc[k].dt = r.dt;
         sc[k].H_n = r.H_n;
         sc[k].A_n = r.A_n;
         sc[k].H0 = r.H0;
@@ -327,9 +399,9 @@ perrk_status perrk_set_resume(perrk_ctx *h, const perrk_resume_info *in, void *s
         sc[k].nsteps_done = (int32_t)r.steps;
     }
     PERRK_CUDA(cudaMemcpyAsync(c.g_scal, sc.data(), sc.size() * sizeof(InstScalars), cudaMemcpyHostToDevice, st),
-               "resume upload");
-    PERRK_CUDA(cudaStreamSynchronize(st), "resume sync");
-    h->host_steps = in[0].steps;
+               "checkpoint scalars");
+    PERRK_CUDA(cudaStreamSynchronize(st), "checkpoint sync");
+    h->host_steps = rs[0].steps;
     return PERRK_OK;
 }
 

@@ -47,14 +47,16 @@ def test_resumed_run_is_bitwise_identical(precision, guess, target):
     rec_a = a.step(3)
     ckpt = a.checkpoint()
     a.close()
-    assert all(h.steps == 3 for h in ckpt[1])
+    hd, hist = pk.checkpoint_history(ckpt)
+    assert hd.magic == 0x4b435250 and hd.precision == precision and hd.n_inst == 2
+    assert all(h.steps == 3 for h in hist)
 
     b = pk.Solver(_problems(), opts())
     b.set_mlp(w)
     b.resume(ckpt)
     rec_b = b.step(4)
     u_b = b.state()
-    hist = pk.perrk_get_resume(b.h)
+    _, hist = pk.checkpoint_history(b.checkpoint())
     b.close()
 
     assert np.array_equal(u_b, u_ref)
@@ -62,11 +64,25 @@ def test_resumed_run_is_bitwise_identical(precision, guess, target):
     assert all(h.steps == 7 for h in hist)
 
 
-def test_resume_rejects_mismatched_history():
+def test_checkpoint_rejects_mismatch():
+    """A checkpoint loads only into a context of the same precision and
+    shapes, and only with consistent step counts; the context is unchanged
+    after a refused load."""
     s = pk.Solver(_problems(), pk.options())
-    hist = pk.perrk_get_resume(s.h)
-    hist[1].steps = hist[0].steps + 1
+    data = bytearray(s.checkpoint())
+    u0 = s.state()
+    other = pk.Solver(_problems(), pk.options(precision=pk.MIXED))
     with pytest.raises(pk.PerrkError) as ei:
-        pk.perrk_set_resume(s.h, hist)
+        other.resume(bytes(data))
     assert ei.value.status == pk.PERRK_INVALID_ARG
+    other.close()
+    bad = bytearray(data)
+    off = pk.C.sizeof(pk.perrk_checkpoint_header) + pk.C.sizeof(pk.perrk_resume_info) + \
+        pk.perrk_resume_info.steps.offset
+    bad[off:off + 8] = (5).to_bytes(8, "little")          # instance 1 at another step count
+    with pytest.raises(pk.PerrkError):
+        s.resume(bytes(bad))
+    with pytest.raises(pk.PerrkError):
+        s.resume(bytes(data[:-8]))                         # truncated
+    assert np.array_equal(s.state(), u0)
     s.close()

@@ -52,6 +52,8 @@ class Workload:
     surface_flux: str        # "ec" | "es_rusanov"
     gamma_gas: float = GAMMA_GAS
     info: dict = dataclasses.field(default_factory=dict)
+    mu: float = 0.0          # dynamic viscosity (0: inviscid Euler)
+    prandtl: float = 0.75    # Prandtl number of the viscous runs
 
     @property
     def n_elem(self):
@@ -192,6 +194,30 @@ def taylor_green(x, y, z, mach=0.1, gamma=GAMMA_GAS):
     vz = np.zeros_like(x)
     p = 1.0 / (gamma * mach ** 2) + (np.cos(2 * x) + np.cos(2 * y)) * (np.cos(2 * z) + 2.0) / 16.0
     return prim_to_cons(np.ones_like(x), np.stack([vx, vy, vz]), p, gamma)
+
+
+def viscous_shock_prims(s, gamma=5.0 / 3.0, mu=0.15, rho0=1.0, vs=1.0):
+    """Traveling viscous shock of Sec. 4.2 (eq. ViscousShockSolution) at the
+    signed distance s = x0 along the shock normal (x0 = x - v t), for the
+    Mach number Ma = 2 / sqrt(3 - gamma) at which the profile is explicit:
+    c0 = v / Ma, p0 = c0^2 rho0 / gamma, chi = 2 exp(s / (2 l)),
+    w = 1 + (1 - sqrt(1 + 2 chi^2)) / (2 chi^2);  rho = rho0 / w,
+    u = v (1 - w), p = p0 / w (1 + (gamma - 1) / 2 Ma^2 (1 - w^2)).
+    This w solves dw/ds = -(w - 1)(w - 1/2) / (l w).  The momentum balance of
+    the Navier-Stokes-Fourier equations across the profile (Stokes'
+    hypothesis; Pr = 3/4 keeps the total enthalpy constant) requires
+    l = 8 gamma mu / (3 (gamma + 1) rho0 v), which is taken here: the printed
+    length mu / (gamma-1) * 2 gamma / (gamma-1) / (rho0 v) is larger by
+    2 / (gamma - 1)^2 (4.5 at gamma = 5/3), and with it the profile is not a
+    solution at the stated viscosity.
+    s may be complex (complex-step derivatives).  Returns (rho, u_n, p)."""
+    ma = 2.0 / math.sqrt(3.0 - gamma)
+    c0 = vs / ma
+    p0 = c0 * c0 * rho0 / gamma
+    ell = 8.0 * gamma * mu / (3.0 * (gamma + 1.0) * rho0 * vs)
+    chi = 2.0 * np.exp(s / (2.0 * ell))
+    w = 1.0 + (1.0 - np.sqrt(1.0 + 2.0 * chi * chi)) / (2.0 * chi * chi)
+    return rho0 / w, vs * (1.0 - w), p0 / w * (1.0 + 0.5 * (gamma - 1.0) * ma * ma * (1.0 - w * w))
 
 
 def to_soa(u_nodes):
@@ -340,7 +366,7 @@ def khi_2d(n=256, seed=1, E=(16, 10, 7, 5), order=4, n_levels=4, fine_counts=Non
                     "ec_ranocha", "es_rusanov", info=dict(phase=phase, hx=hx))
 
 
-def tgv_3d(n=64, n_fine=16, E=(8, 4), order=3, cfl=0.5):
+def tgv_3d(n=64, n_fine=16, E=(8, 4), order=3, cfl=0.5, mu=0.0):
     """Taylor-Green vortex on [0, 2 pi]^3, n^3 affine boxes, the central n_fine
     cells per axis at half width (partition by shortest edge: cross of slabs)."""
     nc = n - n_fine
@@ -356,10 +382,29 @@ def tgv_3d(n=64, n_fine=16, E=(8, 4), order=3, cfl=0.5):
     c = math.sqrt(1.0 / 0.01)  # speed of sound for Ma = 0.1, rho = 1
     dt = cfl * (hc / 2) / (2 * N_POLY + 1) / (c + 1.0)
     return Workload(f"tgv3d_{n}^3", 3, "euler3d", coords, faces, part, list(E), order, to_soa(u0), dt,
-                    "ec_ranocha", "ec", info=dict(hc=hc))
+                    "ec_ranocha", "ec", info=dict(hc=hc), mu=mu)
 
 
-def small_box_2d(n=8, seed=0, R=2, E=(6, 3), order=3, ic="vortex", surface="es_rusanov", random_parts=False):
+def viscous_shock_2d(n=16, angle=0.0, L=2.0, gamma=5.0 / 3.0, mu=0.15, E=(4,), order=2):
+    """The viscous shock of Sec. 4.2 on the periodic square [-L, L]^2 of n x n
+    boxes, its normal rotated by `angle` in the plane (the state jumps across
+    the periodic seams; away from them it is the traveling profile)."""
+    e = np.linspace(-L, L, n + 1)
+    coords = tensor_coords([e, e])
+    faces = structured_faces([n, n])
+    nrm = np.array([math.cos(angle), math.sin(angle)])
+    sx = coords[:, :, 0] * nrm[0] + coords[:, :, 1] * nrm[1]
+    rho, un, p = viscous_shock_prims(sx, gamma, mu)
+    u0 = prim_to_cons(rho, un[None] * nrm[:, None, None], p, gamma)
+    h = 2 * L / n
+    dt = 0.035 * (h / (N_POLY + 1)) ** 2
+    part = np.zeros(n * n, np.int32)
+    return Workload(f"viscous_shock2d_{n}", 2, "euler2d", coords, faces, part, list(E), order, to_soa(u0), dt,
+                    "ec_ranocha", "es_rusanov", gamma_gas=gamma, info=dict(angle=angle, L=L, normal=nrm), mu=mu,
+                    prandtl=0.75)
+
+
+def small_box_2d(n=8, seed=0, R=2, E=(6, 3), order=3, ic="vortex", surface="es_rusanov", random_parts=False, mu=0.0):
     """Small tensor mesh on [-L, L]^2 for tests, optionally with random partition ids."""
     rng = np.random.default_rng(BASE_SEED + 7 + 1000 * seed)
     L = 5.0
@@ -377,7 +422,7 @@ def small_box_2d(n=8, seed=0, R=2, E=(6, 3), order=3, ic="vortex", surface="es_r
         u0 = kelvin_helmholtz(coords[:, :, 0] / L, coords[:, :, 1] / L, phase=rng.uniform(0, 6.28))
     dt = 0.2 * hmin.min() / (2 * N_POLY + 1) / 2.5
     return Workload(f"box2d_{n}", 2, "euler2d", coords, faces, part, list(E), order, to_soa(u0), dt,
-                    "ec_ranocha", surface)
+                    "ec_ranocha", surface, mu=mu)
 
 
 def batched_2d(n_inst=256, seed=1, n_min=16, n_max=128, S=12, order=3):
