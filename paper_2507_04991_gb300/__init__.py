@@ -46,7 +46,8 @@ class perrk_mesh_desc(C.Structure):
 class perrk_scheme_desc(C.Structure):
     _fields_ = [("order", C.c_int), ("S", C.c_int), ("R", C.c_int), ("E", C.c_void_p), ("c", C.c_void_p),
                 ("b", C.c_void_p), ("a1", C.c_void_p), ("asub", C.c_void_p), ("equation", C.c_int),
-                ("gamma_gas", C.c_double), ("volume_flux", C.c_int), ("surface_flux", C.c_int)]
+                ("gamma_gas", C.c_double), ("volume_flux", C.c_int), ("surface_flux", C.c_int),
+                ("mu", C.c_double), ("prandtl", C.c_double)]
 
 
 class perrk_options(C.Structure):
@@ -184,7 +185,7 @@ def mesh_desc(coords, faces, part, keep):
     return m
 
 
-def scheme_desc(order, E, c, b, a1, asub, equation, surface_flux, gamma_gas, keep):
+def scheme_desc(order, E, c, b, a1, asub, equation, surface_flux, gamma_gas, keep, mu=0.0, prandtl=0.75):
     E = np.ascontiguousarray(E, dtype=np.int32)
     s = perrk_scheme_desc()
     s.order = int(order)
@@ -199,6 +200,8 @@ def scheme_desc(order, E, c, b, a1, asub, equation, surface_flux, gamma_gas, kee
     s.gamma_gas = float(gamma_gas)
     s.volume_flux = VOLUME_EC
     s.surface_flux = int(surface_flux)
+    s.mu = float(mu)
+    s.prandtl = float(prandtl)
     return s
 
 
@@ -518,7 +521,8 @@ class Solver:
             meshes.append(mesh_desc(pb.coords, pb.faces, pb.part, self.keep))
             tab = tableaux[k] if tableaux else perrk_build_tableau(pb.order, pb.E)
             schemes.append(scheme_desc(pb.order, pb.E, *tab, EQUATION_CODES[pb.equation],
-                                       SURFACE_CODES[pb.surface_flux], pb.gamma_gas, self.keep))
+                                       SURFACE_CODES[pb.surface_flux], pb.gamma_gas, self.keep,
+                                       getattr(pb, "mu", 0.0), getattr(pb, "prandtl", 0.75)))
         self.opts = opts or options()
         self.h = perrk_create_batched(meshes, schemes, self.opts)
         self.n_elem, self.nvar, self.np, self.n_inst = perrk_shape(self.h)

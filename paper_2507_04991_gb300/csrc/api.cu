@@ -57,7 +57,8 @@ static void free_ctx(Ctx &c) {
     void *ptrs[] = {c.g_box_tab, c.U, c.K1, c.Ka, c.Kb, c.d, c.Uf, c.Ul, c.dh, c.dl, c.e_dhf, c.g_wJ_lo, c.K1f, c.Kaf, c.Kbf, c.e_dh, c.g_node, c.g_elem, c.g_fnorm, c.g_wJ, c.g_nbr, c.g_gp,
                     c.g_elist, c.g_chunk_inst, c.g_chunk_e0, c.g_chunk_e1, c.g_inst_chunk0, c.g_inst_nchunks,
                     c.g_coef, c.g_coef_f, c.g_scal, c.g_partials, c.g_counters, c.g_flags, c.g_records, c.g_mlp,
-                    c.g_dftab, c.g_node_f, c.g_elem_f, c.g_fnorm_f, c.g_wJ_f};
+                    c.g_dftab, c.g_node_f, c.g_elem_f, c.g_fnorm_f, c.g_wJ_f, c.g_ring, c.visc_fv,
+                    c.visc_kv};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c.graph_exec) cudaGraphExecDestroy((cudaGraphExec_t)c.graph_exec);
@@ -85,8 +86,6 @@ static perrk_status alloc_ctx(Ctx &c) {
     make_chunks(c, sms);
     const size_t nstate = (size_t)c.V * c.n_elem * c.NP;
     const bool mixed = c.opt.precision == PERRK_MIXED;
-    // float64: U, K_1, two stage registers, d; mixed: float64 U and d, FP32 copy of
-    // U_n and FP32 stage registers (K is an FP32 result in that form)
     // float64 form: U, K_1, two stage registers, d.  Mixed form: U and d as
     // float pairs (hi, lo), FP32 stage registers, U (float64) as the staging
     // buffer of set_state / get_state.
@@ -124,6 +123,15 @@ static perrk_status alloc_ctx(Ctx &c) {
     PERRK_TRY(upload(c.g_nbr, c.nbr, "neighbours"));
     PERRK_TRY(upload(c.g_gp, c.gp_of_elem, "partitions"));
     PERRK_TRY(upload(c.g_elist, c.elist, "element list"));
+    if (c.viscous) {
+        PERRK_TRY(upload(c.g_ring, c.ring, "viscous rings"));
+        const size_t wsz = mixed ? sizeof(float) : sizeof(double);
+        const size_t nn = (size_t)c.n_elem * c.NP * (c.V - 1);
+        PERRK_CUDA(cudaMalloc(&c.visc_fv, nn * c.dim * wsz), "viscous alloc");
+        PERRK_CUDA(cudaMalloc(&c.visc_kv, nn * wsz), "viscous alloc");
+        PERRK_CUDA(cudaMemset(c.visc_fv, 0, nn * c.dim * wsz), "viscous clear");
+        PERRK_CUDA(cudaMemset(c.visc_kv, 0, nn * wsz), "viscous clear");
+    }
     PERRK_TRY(upload(c.g_chunk_inst, c.chunk_inst, "chunks"));
     PERRK_TRY(upload(c.g_chunk_e0, c.chunk_e0, "chunks"));
     PERRK_TRY(upload(c.g_chunk_e1, c.chunk_e1, "chunks"));

@@ -102,6 +102,8 @@ struct Ctx {
     int dim = 0, NP = 0, V = 0, n_elem = 0, n_inst = 0, S = 0, p = 0, n_gp = 0;
     int equation = 0, surface = 0;
     double gamma_gas = 1.4;
+    bool viscous = false;                     // Navier-Stokes-Fourier viscous terms (BR1)
+    double mu = 0.0, prandtl = 0.75;
     bool curved = false;
     perrk_options opt{};
     std::vector<Instance> inst;
@@ -109,6 +111,8 @@ struct Ctx {
     std::vector<int32_t> E_of_gp;             // [n_gp]
     std::vector<int32_t> elist;               // elements sorted by E descending
     std::vector<int32_t> n_active;            // [S] active prefix length per stage
+    std::vector<int32_t> ring, ring_off;      // viscous: per stage the inactive face neighbours of the active
+                                              // prefix (their gradients enter the active viscous fluxes)
     std::vector<int32_t> any_b;               // [S] 1 if some instance has b_i != 0
     std::vector<int32_t> d_read;              // [S] 1 if some instance adds to an existing d at this stage
     bool d_fused = false;                     // every instance: b_i != 0 only at its first, penultimate, last stage
@@ -135,7 +139,9 @@ struct Ctx {
     double *g_node = nullptr, *g_elem = nullptr, *g_fnorm = nullptr, *g_wJ = nullptr;
     float *g_node_f = nullptr, *g_elem_f = nullptr, *g_fnorm_f = nullptr, *g_wJ_f = nullptr;
     float *g_wJ_lo = nullptr;                 // mixed form: omega J = g_wJ_f + g_wJ_lo
-    int32_t *g_nbr = nullptr, *g_gp = nullptr, *g_elist = nullptr;
+    int32_t *g_nbr = nullptr, *g_gp = nullptr, *g_elist = nullptr, *g_ring = nullptr;
+    void *visc_fv = nullptr;                  // viscous: node fluxes [dim][V-1][n_elem * NP] (kernel precision)
+    void *visc_kv = nullptr;                  // viscous: + div f_v of the active elements [V-1][n_elem * NP]
     int32_t *g_chunk_inst = nullptr, *g_chunk_e0 = nullptr, *g_chunk_e1 = nullptr;
     int32_t *g_inst_chunk0 = nullptr, *g_inst_nchunks = nullptr;
     StageCoef *g_coef = nullptr;              // [S][n_gp]

@@ -99,6 +99,11 @@ perrk_status build_ctx(Ctx &c, int n, const perrk_mesh_desc *mesh, const perrk_s
     if (s0.surface_flux != PERRK_SURFACE_EC && s0.surface_flux != PERRK_SURFACE_ES_RUSANOV) return fail("unknown surface flux");
     if (s0.volume_flux != PERRK_VOLUME_EC) return fail("unknown volume flux");
     if (eq != PERRK_BURGERS_1D && !(s0.gamma_gas > 1.0)) return fail("gamma_gas must be > 1");
+    if (!(s0.mu >= 0.0) || !std::isfinite(s0.mu)) return fail("mu must be finite and >= 0");
+    if (s0.mu > 0.0) {
+        if (eq != PERRK_EULER_2D && eq != PERRK_EULER_3D) return fail("viscous terms need the 2D or 3D Euler equations");
+        if (!(s0.prandtl > 0.0) || !std::isfinite(s0.prandtl)) return fail("prandtl must be finite and > 0");
+    }
     if (opts->precision != PERRK_FP64 && opts->precision != PERRK_MIXED) return fail("unknown precision");
     if (opts->newton_max_it < 0 || opts->newton_max_it > 64) return fail("newton_max_it out of range [0, 64]");
     if (!(opts->newton_tol_r >= 0.0) || !(opts->newton_tol_g >= 0.0)) return fail("negative Newton tolerance");
@@ -114,6 +119,9 @@ perrk_status build_ctx(Ctx &c, int n, const perrk_mesh_desc *mesh, const perrk_s
     c.equation = eq;
     c.surface = s0.surface_flux;
     c.gamma_gas = eq == PERRK_BURGERS_1D ? 1.4 : s0.gamma_gas;
+    c.viscous = s0.mu > 0.0;
+    c.mu = s0.mu;
+    c.prandtl = c.viscous ? s0.prandtl : 0.75;
     c.opt = *opts;
     c.p = s0.order;
     c.n_inst = n;
@@ -127,8 +135,8 @@ perrk_status build_ctx(Ctx &c, int n, const perrk_mesh_desc *mesh, const perrk_s
         const perrk_mesh_desc &m = mesh[k];
         const perrk_scheme_desc &sc = scheme[k];
         if (m.dim != dim || sc.equation != eq || sc.surface_flux != s0.surface_flux || sc.order != s0.order ||
-            sc.gamma_gas != s0.gamma_gas)
-            return fail("instances must share dim, equation, fluxes, gamma_gas and order");
+            sc.gamma_gas != s0.gamma_gas || sc.mu != s0.mu || (s0.mu > 0.0 && sc.prandtl != s0.prandtl))
+            return fail("instances must share dim, equation, fluxes, gamma_gas, viscosity and order");
         if (m.N != 3) return fail("only N = 3 is supported");
         if (m.n_elem <= 0 || !m.node_coords || !m.faces || !m.partition_id) return fail("empty mesh or null arrays");
         if (m.n_faces != m.n_elem * dim) return fail("n_faces must equal n_elem * dim");
@@ -379,6 +387,34 @@ perrk_status build_ctx(Ctx &c, int n, const perrk_mesh_desc *mesh, const perrk_s
             if (i == 1 || i >= S - E + 2) ++cnt;
         }
         c.n_active[i - 1] = cnt;
+    }
+    // viscous runs: at each stage the inactive face neighbours of the active
+    // prefix (a ring), whose BR1 gradients enter the active elements' viscous
+    // interface fluxes; sorted by element for locality
+    c.ring.clear();
+    c.ring_off.assign(S + 1, 0);
+    if (c.viscous) {
+        std::vector<int32_t> pos(NE);
+        for (size_t j = 0; j < NE; ++j) pos[c.elist[j]] = (int32_t)j;
+        std::vector<char> mark(NE, 0);
+        for (int i = 0; i < S; ++i) {
+            c.ring_off[i] = (int32_t)c.ring.size();
+            std::vector<int32_t> r;
+            for (int j = 0; j < c.n_active[i]; ++j) {
+                const size_t e = (size_t)c.elist[j];
+                for (int f = 0; f < NF; ++f) {
+                    const int32_t nb = c.nbr[e * NF + f];
+                    if (pos[nb] >= c.n_active[i] && !mark[nb]) {
+                        mark[nb] = 1;
+                        r.push_back(nb);
+                    }
+                }
+            }
+            std::sort(r.begin(), r.end());
+            for (int32_t nb : r) mark[nb] = 0;
+            c.ring.insert(c.ring.end(), r.begin(), r.end());
+        }
+        c.ring_off[S] = (int32_t)c.ring.size();
     }
     // fused direction: with b_i != 0 only at the first, penultimate and last
     // stage (all archetypes), d = b_1 K_1 + b_m K_{S-1} + b_S K_S is formed at

@@ -42,6 +42,15 @@ struct StageParams {
     const float *g_node_f, *g_elem_f, *fnorm_f, *wJ_f;   // FP32 geometry (mixed form)
     const void *box_tab;        // box kernels: per-node work table (NodeTable rows, built on the host)
     double gamma_gas;
+    // viscous (Navier-Stokes-Fourier, BR1): the gradient set of a stage is
+    // the active prefix plus ring[0 .. n_ring); node fluxes in visc_fv
+    // [dim][V-1][NE NP], + div f_v of the active elements in visc_kv
+    // [V-1][NE NP] (kernel precision), added by the stage kernel when set
+    const int32_t *ring;
+    int n_ring;
+    void *visc_fv, *visc_kv;
+    double mu, kappa;           // kappa = mu gamma / ((gamma - 1) Pr)
+    float mu_f, kappa_f;
     double D[16];
     double w_end;
     float Df[16];               // FP32 copies of the tables and constants (mixed form)
@@ -459,9 +468,11 @@ __global__ void __launch_bounds__(EPB * ipow4(DIM), stage_min_blocks<DIM, Real, 
             }
         }
         Real Kr[V];
+        const Real *kv = static_cast<const Real *>(P.visc_kv);
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             Kr[v] = -acc[v] * invJ;
+            if (EQ == EQ_EULER && v > 0 && kv) Kr[v] += kv[(size_t)(v - 1) * NPtot + idx];
             if (!isfinite(Kr[v])) bad |= PERRK_FLAG_NONFINITE;
             if (valid) {
                 if constexpr (sizeof(Real) == 8) P.Kout[v * NPtot + idx] = Kr[v];

@@ -13,6 +13,7 @@ cudaError_t stage_launch_2d(const StageParams &, bool, bool, bool, int, int, cud
 cudaError_t stage_launch_3d(const StageParams &, bool, bool, bool, int, int, cudaStream_t);
 cudaError_t stage_launch_box_2d(const StageParams &, int, bool, int, cudaStream_t);
 cudaError_t stage_launch_box_3d(const StageParams &, int, bool, int, cudaStream_t);
+cudaError_t visc_launch(const StageParams &, int, bool, bool, cudaStream_t);
 
 int default_epb(int dim) { return dim == 1 ? 32 : (dim == 2 ? 8 : 2); }
 
@@ -110,6 +111,20 @@ perrk_status launch_stage(Ctx &c, int stage, bool rhs_only, const double *in_u, 
     P.wJ_f = c.g_wJ_f;
     P.box_tab = c.g_box_tab;
     P.flags = c.g_flags;
+    if (c.viscous) {
+        P.ring = c.g_ring ? c.g_ring + (rhs_only ? 0 : c.ring_off[stage]) : nullptr;
+        P.n_ring = rhs_only ? 0 : c.ring_off[stage + 1] - c.ring_off[stage];
+        P.visc_fv = c.visc_fv;
+        P.visc_kv = c.visc_kv;
+        P.mu = c.mu;
+        P.kappa = c.mu * c.gamma_gas / ((c.gamma_gas - 1.0) * c.prandtl);
+        P.mu_f = (float)P.mu;
+        P.kappa_f = (float)P.kappa;
+        if (!P.visc_fv || !P.visc_kv || (P.n_ring > 0 && !P.ring)) {
+            set_error("viscous buffers missing");
+            return PERRK_INVALID_ARG;
+        }
+    }
     if (P.n_active <= 0) return PERRK_OK;
     if (c.curved && c.dim != 2) {
         set_error("curved geometry is only implemented in 2D");
@@ -123,10 +138,16 @@ perrk_status launch_stage(Ctx &c, int stage, bool rhs_only, const double *in_u, 
     const bool burgers = c.equation == PERRK_BURGERS_1D;
     // mixed form on box elements: kernel variant 0 = the generic stage kernel,
     // 1 = the float4 box kernel, 2 = the box kernel with cp.async staging
-    const bool box = mixed && !burgers && !c.curved && c.dim >= 2 && c.stage_variant > 0;
+    const bool box = mixed && !burgers && !c.curved && c.dim >= 2 && c.stage_variant > 0 && !c.viscous;
     if (box && !c.g_box_tab) {
         set_error("box stage kernel: node table missing");
         return PERRK_INVALID_ARG;
+    }
+    if (c.viscous) {
+        // viscous fluxes over the gradient set, their divergence over the
+        // active prefix; the stage kernel then adds it to K_i
+        cudaError_t ev = visc_launch(P, c.dim, mixed, c.curved, (cudaStream_t)stream);
+        if (ev != cudaSuccess) return cuda_check((int)ev, "viscous launch");
     }
     const int epb = c.stage_epb > 0 ? c.stage_epb : default_epb(c.dim);
     const int groups = (P.n_active + epb - 1) / epb;

@@ -259,7 +259,7 @@ def _radial_contraction(X, Y, R0=6.0, B=0.75):
     return X * fac, Y * fac
 
 
-def vortex_2d(n=64, L=10.0, seed=1, n_levels=3, E=(12, 6, 3), order=3, cfl=0.5, mixed_note=None):
+def vortex_2d(n=64, L=10.0, seed=1, n_levels=3, E=(12, 6, 3), order=3, cfl=0.5, mixed_note=None, mu=0.0):
     """Isentropic vortex on an n x n periodic curvilinear mesh of [-L, L]^2: a
     central patch contracted by 4 (two refinement levels), then a seeded
     smooth periodic displacement of at most 10% of the logical cell size."""
@@ -294,7 +294,7 @@ def vortex_2d(n=64, L=10.0, seed=1, n_levels=3, E=(12, 6, 3), order=3, cfl=0.5, 
     dt = cfl * (H / 4) / (2 * N_POLY + 1) / 2.5
     return Workload(f"vortex2d_{n}x{n}", 2, "euler2d", coords, faces, part, list(E), order, to_soa(u0), dt,
                     "ec_ranocha", "es_rusanov",
-                    info=dict(center=center, strength=strength, L=L, H=H, perturb_k=k, perturb_phase=ph))
+                    info=dict(center=center, strength=strength, L=L, H=H, perturb_k=k, perturb_phase=ph), mu=mu)
 
 
 def graded_edges(n, lo, hi, bands, n_levels, fine_counts):
