@@ -71,14 +71,17 @@ class StepRecord:
 
 
 class Solver:
-    def __init__(self, wl, opts=None, p=None, E=None):
+    def __init__(self, wl, opts=None, p=None, E=None, alphas=None):
         self.wl = wl
         self.phys = physics.Physics(wl.equation, wl.surface_flux, wl.gamma_gas, getattr(wl, "mu", 0.0),
                                     getattr(wl, "prandtl", 0.75))
         self.geo = dgsem.Geometry(wl.coords, wl.faces)
         self.p = p or wl.order
         self.E = list(E or wl.E)
-        self.c, self.b, self.As = tableau.family(self.p, self.E)
+        if alphas is None:
+            self.c, self.b, self.As = tableau.family(self.p, self.E)
+        else:                      # members with the given stability polynomials
+            self.c, self.b, self.As = tableau.family_from_poly(self.p, self.E, alphas)
         self.S = len(self.b)
         self.part = np.asarray(wl.part)
         self.opts = opts or NewtonOptions()

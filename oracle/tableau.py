@@ -198,3 +198,84 @@ def stability_coeffs(b, A):
         out.append(float(b @ v))
         v = A @ v
     return np.array(out)
+
+
+# ------------------------------------------- members from a stability polynomial ---
+
+def _set_chain(A, c, m, a):
+    """Row m (1-based) with K_{m-1} coefficient a and K_1 coefficient c_m - a."""
+    A[m - 1, m - 2] = a
+    A[m - 1, 0] = c[m - 1] - a
+
+
+def _solve_row(A, c, b, m, j, target):
+    """Set row m so that alpha_j = b^T A^{j-1} 1 equals target; alpha_j is
+    affine in that row's entry (one evaluation at 0 and one at 1)."""
+    _set_chain(A, c, m, 0.0)
+    f0 = stability_coeffs(b, A)[j]
+    _set_chain(A, c, m, 1.0)
+    f1 = stability_coeffs(b, A)[j]
+    a = (target - f0) / (f1 - f0)
+    _set_chain(A, c, m, a)
+    return a
+
+
+def member_from_poly(p, S, E, alpha):
+    """Member with E evaluations whose stability polynomial has the
+    coefficients alpha[k], k = 0..E (alpha_k = 1/k! for k <= p; the E - p
+    others free, Sec. 2.2), in the archetype's structure.
+
+    p = 2: alpha_j fixes row S - j + 3, taken from the last row upwards.
+    p = 3: for a trial t = a_{S-1,S-2} (row S then (1 - t)/4 by the order-3
+    condition) alpha_j, j = 4 .. E-1, fixes row S - j + 2 in turn; alpha_E is
+    then a scalar equation in t.  Of its roots on [-3, 3] the one nearest the
+    default 1/4 is taken (a reading: the polynomial does not fix the chain
+    uniquely).  p = 4 is not supported (its base stages fix one coefficient).
+    Every coefficient is evaluated from the full Butcher matrix."""
+    c, b = abscissae(p, S), weights(p, S)
+    A = member(p, S, E)
+    first = S - E + 2
+    alpha = np.asarray(alpha, dtype=float)
+    if p == 2:
+        for j in range(3, E + 1):
+            _solve_row(A, c, b, S - j + 3, j, alpha[j])
+        return A
+    if p != 3:
+        raise NotImplementedError("p = 4")
+    if E <= 3:
+        return A
+
+    A0 = A.copy()
+
+    def resid(t):
+        A[:] = A0                  # no entry of an earlier trial (possibly non-finite) survives
+        _set_chain(A, c, S - 1, t)
+        _set_chain(A, c, S, (1.0 - t) / 4.0)
+        for j in range(4, E):
+            _solve_row(A, c, b, S - j + 2, j, alpha[j])
+        return stability_coeffs(b, A)[E] - alpha[E]
+
+    ts = np.linspace(-3.0, 3.0, 6001)
+    with np.errstate(all="ignore"):
+        f = np.array([resid(t) for t in ts])
+        roots = []
+        for i in range(len(ts) - 1):
+            if np.isfinite(f[i]) and np.isfinite(f[i + 1]) and f[i] * f[i + 1] <= 0.0:
+                lo, hi, flo = ts[i], ts[i + 1], f[i]
+                for _ in range(200):
+                    mid = 0.5 * (lo + hi)
+                    fm = resid(mid)
+                    if (fm <= 0.0) == (flo <= 0.0):
+                        lo, flo = mid, fm
+                    else:
+                        hi = mid
+                roots.append(0.5 * (lo + hi))
+    if not roots:
+        raise ValueError("no chain of the p = 3 archetype has this stability polynomial")
+    resid(min(roots, key=lambda r: abs(r - 0.25)))
+    return A
+
+
+def family_from_poly(p, E_list, alphas):
+    S = max(E_list)
+    return abscissae(p, S), weights(p, S), [member_from_poly(p, S, E, a) for E, a in zip(E_list, alphas)]
