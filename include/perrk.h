@@ -179,9 +179,16 @@ perrk_status perrk_build_tableau(int p, int R, const int32_t *E, int S_cap, int 
 /* Total elements, variables, nodes per element and instances of ctx. */
 perrk_status perrk_shape(const perrk_ctx *ctx, int *n_elem, int *nvar, int *np, int *n_inst);
 
-/* Copy a state (SoA, float64, n_elem*NP*V values) in (on_device = 0: host
- * memory, 1: device memory).  Resets t = 0, gamma_{n-1} = 1 and sets
- * H_n = H(U_0) = H(u), A_n = sum omega J |s(u)| for every instance. */
+/* Copy a state (SoA, float64, n_elem*NP*V values) in or out.  on_device:
+ *   0  host memory; the call returns when the copy is complete;
+ *   1  device memory (ordered on the stream);
+ *   2  host memory, asynchronous: the copy is enqueued on the stream and the
+ *      call returns at once; the caller keeps the buffer unchanged (set) or
+ *      unread (get) until the stream is synchronised.  With page-locked
+ *      buffers the copies of one context overlap the kernels of another.
+ * set_state resets t = 0, gamma_{n-1} = 1 and sets H_n = H(U_0) = H(u),
+ * A_n = sum omega J |s(u)| for every instance.  INVALID_ARG for any other
+ * on_device value. */
 perrk_status perrk_set_state(perrk_ctx *ctx, const double *u, int on_device, void *stream);
 perrk_status perrk_get_state(perrk_ctx *ctx, double *u, int on_device, void *stream);
 

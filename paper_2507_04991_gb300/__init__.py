@@ -231,24 +231,41 @@ def perrk_shape(h):
     return tuple(x.value for x in v)
 
 
+STATE_HOST, STATE_DEVICE, STATE_HOST_ASYNC = 0, 1, 2
+
+
+def _state_mode(on_device):
+    mode = int(on_device)
+    if mode not in (STATE_HOST, STATE_DEVICE, STATE_HOST_ASYNC):
+        raise ValueError("on_device must be 0 (host), 1 (device) or 2 (host, asynchronous)")
+    return mode
+
+
 def perrk_set_state(h, u, on_device=False, stream=0):
     """u: host float64 ndarray, or a raw pointer (int) to device memory
-    (on_device) or to host memory (e.g. pinned)."""
+    (on_device = 1) or to host memory (0; 2 = asynchronous, e.g. a pinned
+    buffer the caller keeps unchanged until the stream is synchronised)."""
+    mode = _state_mode(on_device)
     if isinstance(u, int):
         ptr, keep = C.c_void_p(u), None
     else:
+        if mode == STATE_HOST_ASYNC:
+            raise ValueError("asynchronous copies need a raw pointer the caller keeps alive")
         keep = np.ascontiguousarray(u, dtype=np.float64)
         ptr = _ptr(keep)
-    _check(load().perrk_set_state(h, ptr, int(bool(on_device)), C.c_void_p(stream)), "perrk_set_state")
+    _check(load().perrk_set_state(h, ptr, mode, C.c_void_p(stream)), "perrk_set_state")
     del keep
 
 
 def perrk_get_state(h, out=None, on_device=False, stream=0):
     """out: host ndarray (allocated when None), or a raw pointer (int) to
     device memory (on_device) or to host memory."""
+    mode = _state_mode(on_device)
     if isinstance(out, int):
-        _check(load().perrk_get_state(h, C.c_void_p(out), int(bool(on_device)), C.c_void_p(stream)), "perrk_get_state")
+        _check(load().perrk_get_state(h, C.c_void_p(out), mode, C.c_void_p(stream)), "perrk_get_state")
         return out
+    if mode == STATE_HOST_ASYNC:
+        raise ValueError("asynchronous copies need a raw pointer the caller keeps alive")
     n_elem, nvar, npn, _ = perrk_shape(h)
     if out is None:
         out = np.empty((nvar, n_elem, npn))

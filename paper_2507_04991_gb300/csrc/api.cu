@@ -259,29 +259,29 @@ perrk_status perrk_shape(const perrk_ctx *h, int *n_elem, int *nvar, int *np, in
 }
 
 perrk_status perrk_set_state(perrk_ctx *h, const double *u, int on_device, void *stream) {
-    if (!h || !u) return PERRK_INVALID_ARG;
+    if (!h || !u || on_device < 0 || on_device > 2) return PERRK_INVALID_ARG;
     Ctx &c = h->c;
     const size_t bytes = (size_t)c.V * c.n_elem * c.NP * sizeof(double);
     cudaStream_t st = (cudaStream_t)stream;
-    PERRK_CUDA(cudaMemcpyAsync(c.U, u, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st),
+    PERRK_CUDA(cudaMemcpyAsync(c.U, u, bytes, on_device == 1 ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st),
                "set_state copy");
     PERRK_CUDA(cudaMemsetAsync(c.g_flags, 0, sizeof(uint32_t), st), "flags clear");
     if (c.Uf) PERRK_TRY(launch_split(c.U, c.Uf, c.Ul, (size_t)c.V * c.n_elem * c.NP, st));
     PERRK_TRY(launch_entropy_set(c, st));
     h->host_steps = 0;
-    if (!on_device) PERRK_CUDA(cudaStreamSynchronize(st), "set_state sync");
+    if (on_device == 0) PERRK_CUDA(cudaStreamSynchronize(st), "set_state sync");
     return PERRK_OK;
 }
 
 perrk_status perrk_get_state(perrk_ctx *h, double *u, int on_device, void *stream) {
-    if (!h || !u) return PERRK_INVALID_ARG;
+    if (!h || !u || on_device < 0 || on_device > 2) return PERRK_INVALID_ARG;
     Ctx &c = h->c;
     const size_t bytes = (size_t)c.V * c.n_elem * c.NP * sizeof(double);
     cudaStream_t st = (cudaStream_t)stream;
     if (c.Uf) PERRK_TRY(launch_join(c.Uf, c.Ul, c.U, (size_t)c.V * c.n_elem * c.NP, st));
-    PERRK_CUDA(cudaMemcpyAsync(u, c.U, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st),
+    PERRK_CUDA(cudaMemcpyAsync(u, c.U, bytes, on_device == 1 ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st),
                "get_state copy");
-    if (!on_device) PERRK_CUDA(cudaStreamSynchronize(st), "get_state sync");
+    if (on_device == 0) PERRK_CUDA(cudaStreamSynchronize(st), "get_state sync");
     return PERRK_OK;
 }
 

@@ -86,3 +86,32 @@ def test_checkpoint_rejects_mismatch():
         s.resume(bytes(data[:-8]))                         # truncated
     assert np.array_equal(s.state(), u0)
     s.close()
+
+
+def test_async_state_copies_match_synchronous():
+    """on_device = 2: asynchronous host copies on a side stream, two contexts
+    in flight at once, give the same result as the synchronous path."""
+    import torch
+    wl = _problems()
+    u0 = np.concatenate([w.u0 for w in wl], axis=1)
+    ref = pk.Solver(wl, pk.options(precision=pk.MIXED))
+    ref.set_state(u0)
+    ref.step(3, info=False)
+    u_ref = ref.state()
+    ref.close()
+    host_in = torch.from_numpy(np.ascontiguousarray(u0)).pin_memory()
+    outs = [torch.empty_like(host_in).pin_memory() for _ in range(2)]
+    ctx = [pk.Solver(wl, pk.options(precision=pk.MIXED)) for _ in range(2)]
+    streams = [torch.cuda.Stream() for _ in range(2)]
+    for X in range(2):
+        s = streams[X].cuda_stream
+        pk.perrk_set_state(ctx[X].h, host_in.data_ptr(), on_device=pk.STATE_HOST_ASYNC, stream=s)
+        pk.perrk_step(ctx[X].h, 3, info=False, stream=s)
+        pk.perrk_get_state(ctx[X].h, outs[X].data_ptr(), on_device=pk.STATE_HOST_ASYNC, stream=s)
+    torch.cuda.synchronize()
+    for X in range(2):
+        assert np.array_equal(outs[X].numpy(), u_ref)
+    with pytest.raises(ValueError):             # an ndarray may not outlive an asynchronous call
+        pk.perrk_set_state(ctx[0].h, u0, on_device=pk.STATE_HOST_ASYNC)
+    for X in range(2):
+        ctx[X].close()
