@@ -76,7 +76,7 @@ def _feasible(z, R, p, E, n_dir, max_rounds=60):
         A_ub = np.concatenate([A_ub, -np.ones((A_ub.shape[0], 1))], axis=1)
         res = linprog(cost, A_ub=A_ub, b_ub=np.zeros(A_ub.shape[0]), A_eq=A_eq, b_eq=b_eq,
                       bounds=[(None, None)] * (E + 2), method="highs")
-        if res.status != 0 or res.x[-1] > 1.0:
+        if res.status != 0 or res.x[-1] > 1.0 + 1e-9:
             return None
         gam = res.x[:-1]
         w = T @ gam
@@ -99,7 +99,7 @@ def stable_step(alpha, lam, h_hi, tol=1e-9, n_grid=4000):
     the spectrum: a descending scan (stability in h need not be monotone on a
     discrete spectrum), then bisection between the first stable grid point
     and the unstable one above it."""
-    lam = np.asarray(lam, dtype=complex)
+    lam = _clean_spectrum(lam)
     coef = np.asarray(alpha)[::-1]
 
     def ok(h):
@@ -121,12 +121,24 @@ def stable_step(alpha, lam, h_hi, tol=1e-9, n_grid=4000):
     return 0.0
 
 
+def _clean_spectrum(spectrum):
+    """Upper half of a conjugate-symmetric spectrum.  Eigenvalues within
+    1e-8 rho of the origin are the conserved modes (P(0) = 1 for every P) and
+    are dropped; real parts in (0, 1e-8 rho] are rounding of a
+    finite-difference Jacobian and are set to 0."""
+    lam = np.asarray(spectrum, dtype=complex)
+    lam = lam[lam.imag >= 0.0]
+    rho = float(np.abs(lam).max()) if lam.size else 0.0
+    lam = lam[np.abs(lam) > 1e-8 * rho]
+    small = (lam.real > 0.0) & (lam.real <= 1e-8 * rho)
+    lam[small] = 1j * lam[small].imag
+    return lam
+
+
 def optimal_polynomial(spectrum, p, E, n_dir=64, rel_tol=1e-4, h_hi=None):
     """(h, alpha): the largest step with |P(h lambda)| <= 1 on the spectrum
     and P's monomial coefficients alpha[0..E] (alpha_k = 1/k! for k <= p)."""
-    lam = np.asarray(spectrum, dtype=complex)
-    lam = lam[lam.imag >= 0.0]                      # conjugate-symmetric spectra
-    lam = lam[np.abs(lam) > 0.0]
+    lam = _clean_spectrum(spectrum)
     if E < p or lam.size == 0:
         raise ValueError("need E >= p and a non-zero spectrum")
     rho = float(np.abs(lam).max())

@@ -110,10 +110,10 @@ def test_optimised_member_stable_where_default_grows():
     s = pk.Solver(wl, pk.options(relaxation=False))
     lam = st.jacobian_spectrum(s, base)
     s.close()
-    h_opt, alpha = st.optimal_polynomial(lam, p, S)
+    h_opt, alpha = st.optimal_polynomial(lam, p, S, n_dir=32, rel_tol=1e-3)
     a_def = T.stability_coeffs(T.weights(p, S), T.member(p, S, S))[:S + 1]
     h_def = st.stable_step(a_def, lam, 2.0 * h_opt)
-    assert h_opt > 1.1 * h_def, (h_opt, h_def)
+    assert h_opt > 2.0 * h_def, (h_opt, h_def)
     dt = h_opt
     rho_opt = np.abs(np.polyval(alpha[::-1], dt * lam)).max()
     rho_def = np.abs(np.polyval(a_def[::-1], dt * lam)).max()

@@ -125,3 +125,31 @@ def test_optimised_family_is_valid(lib):
     for r, E in enumerate(E_list):
         al = T.stability_coeffs(b, As[r])[:E + 1]
         assert np.abs(np.polyval(al[::-1], hs[r] * SPEC)).max() <= 1.0 + 1e-7
+
+
+def test_gain_on_a_dg_spectrum():
+    """The spectrum of the oracle's DGSEM Jacobian (free stream, Ranocha EC
+    volume and Rusanov ES surface fluxes, 4 x 4 periodic boxes): the
+    optimised p = 3, E = 8 polynomial is stable there at a step well above the
+    default member's."""
+    import workloads
+    from oracle import dgsem, physics
+    wl = workloads.small_box_2d(n=4, seed=51, R=1, E=[8], order=3)
+    u = np.empty_like(wl.u0)
+    u[0], u[1], u[2] = 1.0, 0.5, 0.3
+    u[3] = 1.0 / 0.4 + 0.5 * (0.25 + 0.09)
+    geo = dgsem.Geometry(wl.coords, wl.faces)
+    ph = physics.Physics(wl.equation, wl.surface_flux, wl.gamma_gas)
+    f0 = dgsem.rhs(geo, ph, u).ravel()
+    step = 1e-7 * np.abs(u).max()
+    J = np.empty((u.size, u.size))
+    for k in range(u.size):
+        du = u.copy().ravel()
+        du[k] += step
+        J[:, k] = (dgsem.rhs(geo, ph, du.reshape(u.shape)).ravel() - f0) / step
+    lam = np.linalg.eigvals(J)
+    h, alpha = st.optimal_polynomial(lam, 3, 8, n_dir=32, rel_tol=1e-3)
+    a_def = T.stability_coeffs(T.weights(3, 8), T.member(3, 8, 8))[:9]
+    h_def = st.stable_step(a_def, lam, 2.0 * h)
+    assert h > 2.0 * h_def, (h, h_def)
+    assert st.stable_step(alpha, lam, h) == h
