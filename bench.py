@@ -57,6 +57,12 @@ def make_workload(name, rank=0):
     if name == "tgv3d":
         return [workloads.tgv_3d(n=64)], ("Taylor-Green vortex Ma 0.1, 64^3 boxes, central 16 per axis at h/2, "
                                           "N=3, 2 partitions E={8,4}, p=3, EC")
+    if name == "tgv3d_visc":
+        wl = workloads.tgv_3d(n=64, mu=1.0 / 1600.0)
+        wl.prandtl = 0.71
+        return [wl], ("viscous Taylor-Green vortex, Re 1600 (mu = 1/1600), Pr 0.71, Ma 0.1, 64^3 boxes, central 16 "
+                      "per axis at h/2, N=3, 2 partitions E={8,4}, p=3, EC volume and surface fluxes, "
+                      "Navier-Stokes-Fourier viscous terms by BR1 on entropy-variable gradients")
     if name == "burgers1d":
         return [workloads.burgers_1d()], "Burgers 1D, 64 elements (16 at h/4), N=3, p=2 E={8,4}, EC"
     raise SystemExit(f"unknown workload {name}")

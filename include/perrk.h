@@ -283,7 +283,9 @@ perrk_status perrk_launch_stage(perrk_ctx *ctx, int stage, void *stream);
 /* Static facts of one stage launch: elements evaluated and the algorithmic
  * bytes it must move (own-element reads of U_n, K_1, K_{i-1} as the stage
  * rows require, the K_i write, the d read/write at stages with b_i != 0,
- * geometry and index data; neighbour face reads are not counted).  Also the
+ * geometry and index data; neighbour face reads are not counted; with
+ * viscous terms also the BR1 node fluxes of the gradient set and their
+ * divergence).  Also the
  * stages per step, the number of kernels one step launches and the DOF-stage
  * updates (sum_r E^(r) M^(r), eq. RHSEvals) of one step. */
 perrk_status perrk_stage_info(const perrk_ctx *ctx, int stage, int64_t *n_active, int64_t *bytes, int *n_stages,

@@ -646,12 +646,31 @@ perrk_status perrk_stage_info(const perrk_ctx *h, int stage, int64_t *n_active, 
         if (sc.b != 0.0) geo += (int64_t)c.NP * 8 + 8;  // omega J and the element's Delta H slot
         tot += arrays * per_arr + dbytes + geo + 4 * (2 + NF);  // element list, partition id, neighbours
     }
+    if (c.viscous && na > 0) {
+        // BR1: node fluxes over the gradient set (stage state read again, f_v
+        // written), their divergence over the active prefix (f_v read, the
+        // result written and read back by the stage kernel)
+        const int64_t real = c.opt.precision == PERRK_MIXED ? 4 : 8;
+        const int64_t fvb = (int64_t)c.dim * (c.V - 1) * c.NP * real, kvb = (int64_t)(c.V - 1) * c.NP * real;
+        const int64_t geo_v = c.curved ? (int64_t)c.NP * 5 * real + (int64_t)NF * NFP * 2 * real : (int64_t)(c.dim + 1 + NF) * real;
+        const int32_t *ring = c.ring.data() + c.ring_off[stage];
+        const int n_ring = c.ring_off[stage + 1] - c.ring_off[stage];
+        for (int k = 0; k < na + n_ring; ++k) {
+            const int e = k < na ? c.elist[k] : ring[k - na];
+            const StageCoef &sc = coef[(size_t)stage * c.n_gp + c.gp_of_elem[e]];
+            int64_t arrays = 1;
+            if (stage > 0) arrays += 1;
+            if (stage > 0 && sc.asub != 0.0) arrays += 1;
+            tot += arrays * per_arr + fvb + geo_v + 4 * (2 + NF);
+        }
+        tot += (int64_t)na * (fvb + 2 * kvb + geo_v + 4 * (1 + NF));
+    }
     if (n_active) *n_active = na;
     if (bytes) *bytes = tot;
     if (n_stages) *n_stages = c.S;
     if (kernels_per_step) {
         int k = 0;
-        for (int i = 0; i < c.S; ++i) k += c.n_active[i] > 0 ? 1 : 0;
+        for (int i = 0; i < c.S; ++i) k += c.n_active[i] > 0 ? (c.viscous ? 3 : 1) : 0;
         k += 2;  // relax_init + update
         if (c.opt.relaxation)
             k += c.opt.newton_max_it +
