@@ -378,27 +378,30 @@ def run_native(args):
     achieved = st["bytes"] / k_s / 1e9
 
     # ---- end to end through the C ABI with host buffers (pinned): every step
-    # copies its whole input state in and its whole result state out.  Two
-    # contexts take the steps in turn on two streams with asynchronous copies,
-    # so one context's copies run under the other's kernels (the host link
-    # carries both directions at once).
+    # copies its whole input state in and its whole result state out.  Three
+    # contexts take the steps in turn on three streams with asynchronous
+    # copies: a context's chain (copy in, set-up, step, copy out) is about
+    # three steps long, so the host link and the kernels both stay busy.
+    n_ctx = 3
     host_u = torch.from_numpy(np.ascontiguousarray(uc)).pin_memory()
-    host_out = [torch.empty_like(host_u).pin_memory() for _ in range(2)]
+    host_out = [torch.empty_like(host_u).pin_memory() for _ in range(n_ctx)]
     state_bytes = host_u.numel() * 8
-    second = pk.Solver(insts, pk.options(guess=pk.GUESS_MLP, **mixed_opts))
-    pk.perrk_set_tuning(second.h, tuning["elems_per_cta"], tuning["persistent_grid"], tuning["relax_threads"],
-                        tuning["stage_variant"])
-    second.set_mlp(W)
-    ctxs = [chosen, second]
-    streams = [stream, torch.cuda.Stream(device=dev)]
-    for X in range(2):                                     # capture each context's graph outside the timing
+    ctxs = [chosen]
+    for _ in range(n_ctx - 1):
+        extra = pk.Solver(insts, pk.options(guess=pk.GUESS_MLP, **mixed_opts))
+        pk.perrk_set_tuning(extra.h, tuning["elems_per_cta"], tuning["persistent_grid"], tuning["relax_threads"],
+                            tuning["stage_variant"])
+        extra.set_mlp(W)
+        ctxs.append(extra)
+    streams = [stream] + [torch.cuda.Stream(device=dev) for _ in range(n_ctx - 1)]
+    for X in range(n_ctx):                                 # capture each context's graph outside the timing
         pk.perrk_set_state(ctxs[X].h, host_u.data_ptr(), on_device=pk.STATE_HOST_ASYNC, stream=streams[X].cuda_stream)
         pk.perrk_step(ctxs[X].h, 1, info=False, stream=streams[X].cuda_stream)
     torch.cuda.synchronize()
-    e2e_steps = max(4, args.steps // 4)
+    e2e_steps = max(2 * n_ctx, args.steps // 4)
     t0 = time.perf_counter()
     for k in range(e2e_steps):
-        X = k % 2
+        X = k % n_ctx
         sX = streams[X].cuda_stream
         pk.perrk_set_state(ctxs[X].h, host_u.data_ptr(), on_device=pk.STATE_HOST_ASYNC, stream=sX)
         pk.perrk_step(ctxs[X].h, 1, info=False, stream=sX)
@@ -406,8 +409,9 @@ def run_native(args):
     torch.cuda.synchronize()
     e2e_time = reduce_over_ranks(time.perf_counter() - t0, world, "max")
     e2e_value = reduce_over_ranks(dof_stage * e2e_steps, world, "sum") / e2e_time
-    e2e_match = bool(torch.equal(host_out[0], host_out[1]))     # both contexts stepped the same input
-    second.close()
+    e2e_match = all(bool(torch.equal(host_out[0], o)) for o in host_out[1:])   # all contexts stepped the same input
+    for extra in ctxs[1:]:
+        extra.close()
 
     if rank != 0:
         return
@@ -439,7 +443,8 @@ def run_native(args):
         "cpu_baseline": {"value": cpu[0], "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"one oracle step each of the first {cpu[1]} instances ({cpu[2]:.1f} s, numpy float64, one thread)"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes,
-                "pipeline": "2 contexts, 2 streams, asynchronous pinned copies", "results_agree": e2e_match},
+                "pipeline": f"{n_ctx} contexts, {n_ctx} streams, asynchronous pinned copies",
+                "results_agree": e2e_match},
         "gpu_launches": kernels_per_step * args.steps,
         "clocks": clk,
     }
