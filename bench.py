@@ -387,6 +387,15 @@ def run_native(args):
         guesses[gname] = {"passes": passes(r_), "mean_abs_guess_error": guess_err(r_)}
     guesses["fp64_gamma_prev"] = {"passes": passes_plain, "mean_abs_guess_error": guess_err(rp)}
 
+    # ---- phases (the paper reports runtime shares of the relaxation and the
+    # entropy integrand): the S stage launches of a step timed on their own,
+    # the relaxation (relax_init, learned guess, Newton passes, update) as the
+    # rest of the step
+    t_stages = timed(lambda: [pk.perrk_launch_stage(chosen.h, i, stream=sh) for i in range(S)], 10) / 10
+    phases = {"stages_ms": 1e3 * t_stages, "step_ms": 1e3 * t_max / args.steps,
+              "relaxation_ms": max(0.0, 1e3 * (t_max / args.steps - t_stages)),
+              "relaxation_share": max(0.0, 1.0 - t_stages / (t_max / args.steps))}
+
     # ---- dominant kernel: an all-active stage of the chosen form, timed live on the launching stream
     st = pk.perrk_stage_info(chosen.h, S - 1)
     k_s = timed(ranged("stage_all_active", lambda: pk.perrk_launch_stage(chosen.h, S - 1, stream=sh)), 20) / 20
@@ -463,6 +472,7 @@ def run_native(args):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes,
                 "pipeline": f"{n_ctx} contexts, {n_ctx} streams, asynchronous pinned copies",
                 "results_agree": e2e_match},
+        "phases": phases,
         "gpu_launches": kernels_per_step * args.steps,
         "clocks": clk,
     }
