@@ -266,8 +266,8 @@ perrk_status perrk_set_state(perrk_ctx *h, const double *u, int on_device, void 
     PERRK_CUDA(cudaMemcpyAsync(c.U, u, bytes, on_device == 1 ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st),
                "set_state copy");
     PERRK_CUDA(cudaMemsetAsync(c.g_flags, 0, sizeof(uint32_t), st), "flags clear");
-    if (c.Uf) PERRK_TRY(launch_split(c.U, c.Uf, c.Ul, (size_t)c.V * c.n_elem * c.NP, st));
-    PERRK_TRY(launch_entropy_set(c, st));
+    if (c.Uf) PERRK_TRY(launch_split_entropy_set(c, st));
+    else PERRK_TRY(launch_entropy_set(c, st));
     h->host_steps = 0;
     if (on_device == 0) PERRK_CUDA(cudaStreamSynchronize(st), "set_state sync");
     return PERRK_OK;

@@ -40,6 +40,7 @@ struct RelaxParams {
     size_t NE;
     double gamma_gas;
     int max_it, guess, target, relax, query, mixed, solver;
+    int split;             // mixed form, k_entropy: split U (float64) into Uf, Ul first (set_state)
     double tol_r, tol_g, br_lo, br_hi;
     const float4 *dftab;    // double-float log table (mixed form)
     DfConst K;
@@ -566,8 +567,22 @@ __global__ void __launch_bounds__(256) k_entropy(const RelaxParams P) {
     for (size_t j = n0 + threadIdx.x; j < n1; j += blockDim.x) {
         if constexpr (DF) {
             df x[V];
+            if (P.split) {
+                // hi = round(u), lo = round(u - hi): the float pair set_state stores
 #pragma unroll
-            for (int v = 0; v < V; ++v) x[v] = df{__ldg(P.Uf + v * NPtot + j), __ldg(P.Ul + v * NPtot + j)};
+                for (int v = 0; v < V; ++v) {
+                    const size_t i = v * NPtot + j;
+                    const double u = P.U[i];
+                    const float hi = __double2float_rn(u);
+                    const float lo = __double2float_rn(u - (double)hi);
+                    P.Uf[i] = hi;
+                    P.Ul[i] = lo;
+                    x[v] = df{hi, lo};
+                }
+            } else {
+#pragma unroll
+                for (int v = 0; v < V; ++v) x[v] = df{__ldg(P.Uf + v * NPtot + j), __ldg(P.Ul + v * NPtot + j)};
+            }
             float wd;
             const df sv = df_entropy<DIM, EQ>(x, nullptr, P, wd, bad);
             const df t = df_mul(sv, df{__ldg(P.wJf + j), __ldg(P.wJl + j)});
@@ -723,10 +738,13 @@ perrk_status launch_update(Ctx &c, int rec_slot, void *stream) {
 perrk_status launch_entropy(Ctx &c, int query, void *stream) {
     RelaxParams P = relax_params(c);
     P.query = query;
+    P.split = (query == 2 && c.Uf) ? 1 : 0;
+    if (query == 2) P.query = 0;
     run_entropy(c, P, (cudaStream_t)stream, c.relax_threads);
     return cuda_check((int)cudaGetLastError(), "entropy launch");
 }
 
 perrk_status launch_entropy_set(Ctx &c, void *stream) { return launch_entropy(c, 0, stream); }
+perrk_status launch_split_entropy_set(Ctx &c, void *stream) { return launch_entropy(c, 2, stream); }
 
 }  // namespace perrk

@@ -193,6 +193,8 @@ perrk_status launch_relax_init(Ctx &c, void *stream);
 perrk_status launch_newton_pass(Ctx &c, void *stream);
 perrk_status launch_update(Ctx &c, int rec_slot, void *stream);
 perrk_status launch_entropy_set(Ctx &c, void *stream);
+// mixed form: split U into the float pair and set the entropy scalars in one pass
+perrk_status launch_split_entropy_set(Ctx &c, void *stream);
 perrk_status launch_entropy(Ctx &c, int query, void *stream);
 perrk_status launch_mlp_guess(Ctx &c, void *stream);
 size_t box_node_table_2d(const float *Df, void *out);
