@@ -517,9 +517,11 @@ __global__ void __launch_bounds__(EPB * ipow4(DIM), box_min_blocks<DIM, EPB, PIP
             }
         }
         float Kr[V], ksum = 0.0f;
+        const float *kv = static_cast<const float *>(P.visc_kv);   // viscous runs: + div f_v (BR1)
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             Kr[v] = -acc[v] * invJ;
+            if (v > 0 && kv) Kr[v] += kv[(size_t)(v - 1) * NPtot + idx];
             ksum += Kr[v];
         }
         if (!isfinite(ksum)) bad |= PERRK_FLAG_NONFINITE;

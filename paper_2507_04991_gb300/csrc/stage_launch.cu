@@ -138,7 +138,7 @@ perrk_status launch_stage(Ctx &c, int stage, bool rhs_only, const double *in_u, 
     const bool burgers = c.equation == PERRK_BURGERS_1D;
     // mixed form on box elements: kernel variant 0 = the generic stage kernel,
     // 1 = the float4 box kernel, 2 = the box kernel with cp.async staging
-    const bool box = mixed && !burgers && !c.curved && c.dim >= 2 && c.stage_variant > 0 && !c.viscous;
+    const bool box = mixed && !burgers && !c.curved && c.dim >= 2 && c.stage_variant > 0;
     if (box && !c.g_box_tab) {
         set_error("box stage kernel: node table missing");
         return PERRK_INVALID_ARG;

@@ -66,15 +66,17 @@ def test_autotune_keeps_results_bitwise(precision):
 
 
 @pytest.mark.parametrize("dim", [2, 3])
-def test_mixed_stage_kernel_variants_bitwise(dim):
+@pytest.mark.parametrize("mu", [0.0, 0.02])
+def test_mixed_stage_kernel_variants_bitwise(dim, mu):
     """The mixed form's three stage kernels (generic, float4 box kernel, box
     kernel with cp.async staging) under every elements-per-CTA and grid
-    choice give bit-identical steps (same arithmetic in the same order)."""
+    choice give bit-identical steps (same arithmetic in the same order), with
+    and without the viscous terms."""
     if dim == 2:
-        wl = workloads.small_box_2d(n=12, seed=47, R=2, E=[6, 3], order=3, ic="khi")
+        wl = workloads.small_box_2d(n=12, seed=47, R=2, E=[6, 3], order=3, ic="khi", mu=mu)
         epbs = (4, 8, 16)
     else:
-        wl = workloads.tgv_3d(n=8, n_fine=4)
+        wl = workloads.tgv_3d(n=8, n_fine=4, mu=mu)
         epbs = (1, 2, 4)
     ref = None
     for variant in (0, 1, 2):
