@@ -153,3 +153,20 @@ def test_gain_on_a_dg_spectrum():
     h_def = st.stable_step(a_def, lam, 2.0 * h)
     assert h > 2.0 * h_def, (h, h_def)
     assert st.stable_step(alpha, lam, h) == h
+
+
+def test_p4_chain_is_refused():
+    """p = 4's base stages fix one coefficient: no chain from an arbitrary
+    polynomial (the library keeps the default chain)."""
+    c = T.abscissae(4, 8)
+    with pytest.raises(NotImplementedError):
+        st.member_chain(4, c, 8, 8, np.ones(9))
+    with pytest.raises(NotImplementedError):
+        T.member_from_poly(4, 8, 8, np.ones(9))
+
+
+def test_state_copy_modes(lib):
+    assert (pk.STATE_HOST, pk.STATE_DEVICE, pk.STATE_HOST_ASYNC) == (0, 1, 2)
+    for bad in (3, -1):
+        with pytest.raises(ValueError):
+            pk._state_mode(bad)
