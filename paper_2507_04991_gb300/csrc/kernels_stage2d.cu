@@ -43,7 +43,8 @@ cudaError_t stage_launch_2d(const StageParams &P, bool burgers, bool mixed, bool
 template <int EPB, bool PIPE>
 static cudaError_t box_go(const StageParams &P, int grid, cudaStream_t st) {
     if constexpr (stage_box_smem_bytes<2, EPB, PIPE>() <= 48 * 1024) {
-        k_stage_box<2, EPB, PIPE><<<grid, EPB * ipow4(2), 0, st>>>(P);
+        if (P.visc_kv) k_stage_box<2, EPB, PIPE, true><<<grid, EPB * ipow4(2), 0, st>>>(P);
+        else k_stage_box<2, EPB, PIPE, false><<<grid, EPB * ipow4(2), 0, st>>>(P);
         return cudaGetLastError();
     } else {
         return cudaErrorInvalidConfiguration;

@@ -42,7 +42,8 @@ cudaError_t stage_launch_3d(const StageParams &P, bool burgers, bool mixed, bool
 template <int EPB, bool PIPE>
 static cudaError_t box_go(const StageParams &P, int grid, cudaStream_t st) {
     if constexpr (stage_box_smem_bytes<3, EPB, PIPE>() <= 48 * 1024) {
-        k_stage_box<3, EPB, PIPE><<<grid, EPB * ipow4(3), 0, st>>>(P);
+        if (P.visc_kv) k_stage_box<3, EPB, PIPE, true><<<grid, EPB * ipow4(3), 0, st>>>(P);
+        else k_stage_box<3, EPB, PIPE, false><<<grid, EPB * ipow4(3), 0, st>>>(P);
         return cudaGetLastError();
     } else {
         return cudaErrorInvalidConfiguration;

@@ -291,7 +291,9 @@ constexpr int box_min_blocks() {
                     : (EPB * ipow4(DIM) <= 128 ? 768 / (EPB * ipow4(DIM)) : 3);
 }
 
-template <int DIM, int EPB, bool PIPE>
+// VISC: add the viscous divergence visc_kv (Navier-Stokes-Fourier runs); the
+// inviscid instantiation carries no trace of it.
+template <int DIM, int EPB, bool PIPE, bool VISC>
 __global__ void __launch_bounds__(EPB * ipow4(DIM), box_min_blocks<DIM, EPB, PIPE>()) k_stage_box(const StageParams P) {
     using B = BoxShape<DIM>;
     constexpr int NP = B::NP, NF = B::NF, V = B::V, NPAIR = B::NPAIR, PPT = B::PPT;
@@ -517,11 +519,12 @@ __global__ void __launch_bounds__(EPB * ipow4(DIM), box_min_blocks<DIM, EPB, PIP
             }
         }
         float Kr[V], ksum = 0.0f;
-        const float *kv = static_cast<const float *>(P.visc_kv);   // viscous runs: + div f_v (BR1)
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             Kr[v] = -acc[v] * invJ;
-            if (v > 0 && kv) Kr[v] += kv[(size_t)(v - 1) * NPtot + idx];
+            if constexpr (VISC) {
+                if (v > 0) Kr[v] += static_cast<const float *>(P.visc_kv)[(size_t)(v - 1) * NPtot + idx];
+            }
             ksum += Kr[v];
         }
         if (!isfinite(ksum)) bad |= PERRK_FLAG_NONFINITE;
