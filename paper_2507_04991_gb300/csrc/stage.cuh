@@ -471,8 +471,9 @@ __global__ void __launch_bounds__(EPB * ipow4(DIM), stage_min_blocks<DIM, Real, 
         const Real *kv = static_cast<const Real *>(P.visc_kv);
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-            Kr[v] = -acc[v] * invJ;
-            if (EQ == EQ_EULER && v > 0 && kv) Kr[v] += kv[(size_t)(v - 1) * NPtot + idx];
+            // with viscous terms one rounding: fma(-acc, 1/J, div f_v), as in the box kernels
+            if (EQ == EQ_EULER && v > 0 && kv) Kr[v] = dfma(-acc[v], invJ, kv[(size_t)(v - 1) * NPtot + idx]);
+            else Kr[v] = -acc[v] * invJ;
             if (!isfinite(Kr[v])) bad |= PERRK_FLAG_NONFINITE;
             if (valid) {
                 if constexpr (sizeof(Real) == 8) P.Kout[v * NPtot + idx] = Kr[v];

@@ -521,9 +521,12 @@ __global__ void __launch_bounds__(EPB * ipow4(DIM), box_min_blocks<DIM, EPB, PIP
         float Kr[V], ksum = 0.0f;
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-            Kr[v] = -acc[v] * invJ;
             if constexpr (VISC) {
-                if (v > 0) Kr[v] += static_cast<const float *>(P.visc_kv)[(size_t)(v - 1) * NPtot + idx];
+                // one rounding: fma(-acc, 1/J, div f_v), as in the generic kernel
+                Kr[v] = v > 0 ? fmaf(-acc[v], invJ, static_cast<const float *>(P.visc_kv)[(size_t)(v - 1) * NPtot + idx])
+                              : -acc[v] * invJ;
+            } else {
+                Kr[v] = -acc[v] * invJ;
             }
             ksum += Kr[v];
         }
