@@ -163,9 +163,9 @@ def reduce_over_ranks(x, world, op):
 # launch (profiles/k_stage_batched2d_traffic.md).  It is reported only while
 # the stage kernel sources are the ones those captures measured.
 STAGE_TRAFFIC = {"workload": "batched2d",
-                 "bytes": {0: 1597540352 + 1228053504,      # generic kernel, 8 elements per CTA
-                           1: 1597633536 + 1228073728},     # box kernel, 8 elements per CTA
-                 "sources_sha256": "19278bc06f845f1dc39033a5a5005e7b4cb11f14969fe7b5f24b14d1f0d446bd"}
+                 "bytes": {0: 1597573888 + 1228417792,      # generic kernel, 8 elements per CTA
+                           1: 1597730560 + 1228143104},     # box kernel, 8 elements per CTA
+                 "sources_sha256": "772268c2dd644df1b24463eccb6e35a36c4c688c32d62cb83920f13600d02f80"}
 STAGE_SOURCES = ["stage.cuh", "stage_box.cuh", "physics.cuh", "dfloat.cuh", "kernels_stage2d.cu", "stage_launch.cu"]
 
 
