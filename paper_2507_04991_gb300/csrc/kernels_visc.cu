@@ -60,8 +60,16 @@ __device__ __forceinline__ Real normal_comp(const StageParams &P, size_t e, int 
     else return l == k ? Geo<Real>::fn(P, (size_t)e * NF + f) : Real(0);
 }
 
+// Occupancy bound of the 3D mixed-form kernels (registers per thread <= 56,
+// nine CTAs of 128 threads per SM): the neighbour prefetch otherwise raises
+// them to 72 / 64 and costs resident warps.
+template <int DIM, typename Real, int EPB>
+constexpr int visc_min_blocks() {
+    return (DIM == 3 && sizeof(Real) == 4 && EPB * ipow4(DIM) == 128) ? 9 : 1;
+}
+
 template <int DIM, typename Real, bool CURVED, int EPB>
-__global__ void __launch_bounds__(EPB * ipow4(DIM)) k_visc_flux(const StageParams P) {
+__global__ void __launch_bounds__(EPB * ipow4(DIM), visc_min_blocks<DIM, Real, EPB>()) k_visc_flux(const StageParams P) {
     constexpr int NP = ipow4(DIM), NF = 2 * DIM, NFP = ipow4(DIM - 1), V = DIM + 2, VW = DIM + 1;
     __shared__ Real s_w[EPB][VW][NP];
     __shared__ Real s_jump[EPB][NF * NFP][VW];
@@ -89,6 +97,23 @@ __global__ void __launch_bounds__(EPB * ipow4(DIM)) k_visc_flux(const StageParam
         const int e = item < P.n_active ? P.elist[item] : P.ring[item - P.n_active];
         const size_t idx = (size_t)e * NP + q;
 
+        // the neighbour face states this thread needs are formed first, so
+        // that their loads overlap the element's own
+        constexpr int NSLOT = (NF * NFP + NP - 1) / NP;
+        Real wpre[NSLOT][VW];
+#pragma unroll
+        for (int t = 0; t < NSLOT; ++t) {
+            const int sl = q + t * NP;
+            if (sl < NF * NFP) {
+                const int f = sl / NFP, kk = sl % NFP;
+                const int nb = P.nbr[(size_t)e * NF + f];
+                const int qn = face_node_dev<DIM>(f ^ 1, kk);
+                Real un[V], bn, vn[DIM];
+                double t0[V], t1[V], t2[V];
+                stage_state<V, Real>(P, NPtot, (size_t)nb * NP + qn, P.gp[nb], un, t0, t1, t2);
+                visc_wvars<DIM, Real>(un, gm1, wpre[t], bn, vn);
+            }
+        }
         Real u[V], w[VW], beta, vel[DIM];
         {
             double t0[V], t1[V], t2[V];
@@ -100,17 +125,15 @@ __global__ void __launch_bounds__(EPB * ipow4(DIM)) k_visc_flux(const StageParam
         __syncthreads();
 
         // face slots of this element: half jumps (w_nb - w_self) / 2
-        for (int sl = q; sl < NF * NFP; sl += NP) {
-            const int f = sl / NFP, kk = sl % NFP;
-            const int nb = P.nbr[(size_t)e * NF + f];
-            const int qn = face_node_dev<DIM>(f ^ 1, kk);
-            const int qs = face_node_dev<DIM>(f, kk);
-            Real un[V], wn[VW], bn, vn[DIM];
-            double t0[V], t1[V], t2[V];
-            stage_state<V, Real>(P, NPtot, (size_t)nb * NP + qn, P.gp[nb], un, t0, t1, t2);
-            visc_wvars<DIM, Real>(un, gm1, wn, bn, vn);
 #pragma unroll
-            for (int c = 0; c < VW; ++c) s_jump[el][sl][c] = Real(0.5) * (wn[c] - s_w[el][c][qs]);
+        for (int t = 0; t < NSLOT; ++t) {
+            const int sl = q + t * NP;
+            if (sl < NF * NFP) {
+                const int f = sl / NFP, kk = sl % NFP;
+                const int qs = face_node_dev<DIM>(f, kk);
+#pragma unroll
+                for (int c = 0; c < VW; ++c) s_jump[el][sl][c] = Real(0.5) * (wpre[t][c] - s_w[el][c][qs]);
+            }
         }
         __syncthreads();
 
@@ -194,7 +217,7 @@ __global__ void __launch_bounds__(EPB * ipow4(DIM)) k_visc_flux(const StageParam
 }
 
 template <int DIM, typename Real, bool CURVED, int EPB>
-__global__ void __launch_bounds__(EPB * ipow4(DIM)) k_visc_div(const StageParams P) {
+__global__ void __launch_bounds__(EPB * ipow4(DIM), visc_min_blocks<DIM, Real, EPB>()) k_visc_div(const StageParams P) {
     constexpr int NP = ipow4(DIM), NF = 2 * DIM, NFP = ipow4(DIM - 1), VW = DIM + 1;
     __shared__ Real s_F[EPB][DIM][VW][NP];
     const int el = threadIdx.x / NP, q = threadIdx.x % NP;
@@ -208,6 +231,26 @@ __global__ void __launch_bounds__(EPB * ipow4(DIM)) k_visc_div(const StageParams
         const bool valid = slot < P.n_active;
         const int e = P.elist[valid ? slot : P.n_active - 1];
         const size_t idx = (size_t)e * NP + q;
+        const int id[3] = {q & 3, (q >> 2) & 3, (q >> 4) & 3};
+        // neighbours' flux traces at this node's faces, loaded first (boxes
+        // need only the normal component, curved elements all of them)
+        constexpr int NL = CURVED ? DIM : 1;
+        Real fnb[DIM][NL][VW];
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) {
+            const int ik = id[k];
+            if (ik == 0 || ik == 3) {
+                const int fc = 2 * k + (ik == 3 ? 1 : 0);
+                const int nb = P.nbr[(size_t)e * NF + fc];
+                const size_t in = (size_t)nb * NP + face_node_dev<DIM>(fc ^ 1, face_pos<DIM>(q, k));
+#pragma unroll
+                for (int li = 0; li < NL; ++li) {
+                    const int l = CURVED ? li : k;
+#pragma unroll
+                    for (int c = 0; c < VW; ++c) fnb[k][li][c] = fv[(size_t)(l * VW + c) * NPtot + in];
+                }
+            }
+        }
         Real f[DIM][VW];
 #pragma unroll
         for (int l = 0; l < DIM; ++l)
@@ -225,7 +268,6 @@ __global__ void __launch_bounds__(EPB * ipow4(DIM)) k_visc_div(const StageParams
             }
         }
         __syncthreads();
-        const int id[3] = {q & 3, (q >> 2) & 3, (q >> 4) & 3};
         Real acc[VW];
 #pragma unroll
         for (int c = 0; c < VW; ++c) acc[c] = 0;
@@ -248,15 +290,13 @@ __global__ void __launch_bounds__(EPB * ipow4(DIM)) k_visc_div(const StageParams
             if (ik == 0 || ik == 3) {
                 const int fc = 2 * k + (ik == 3 ? 1 : 0);
                 const int kk = face_pos<DIM>(q, k);
-                const int nb = P.nbr[(size_t)e * NF + fc];
-                const size_t in = (size_t)nb * NP + face_node_dev<DIM>(fc ^ 1, kk);
                 const Real sg = (fc & 1) ? Real(0.5) : Real(-0.5);
 #pragma unroll
-                for (int l = 0; l < DIM; ++l) {
+                for (int li = 0; li < NL; ++li) {
+                    const int l = CURVED ? li : k;
                     const Real nu = sg * normal_comp<DIM, Real, CURVED>(P, (size_t)e, fc, kk, l) * inv_w;
-                    if (nu == Real(0)) continue;
 #pragma unroll
-                    for (int c = 0; c < VW; ++c) acc[c] += nu * (fv[(size_t)(l * VW + c) * NPtot + in] - f[l][c]);
+                    for (int c = 0; c < VW; ++c) acc[c] += nu * (fnb[k][li][c] - f[l][c]);
                 }
             }
         }
