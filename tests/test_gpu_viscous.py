@@ -160,3 +160,44 @@ def test_viscous_entropy_decay_and_invariants(precision):
     for v in range(4):
         m0, m1 = geo.integrate(wl.u0[v]), geo.integrate(u[v])
         assert abs(m1 - m0) < tol * (abs(m0) + 1.0)
+
+
+def _edge_case(name):
+    if name == "one_element":
+        # one periodic element: every face pairs it with itself, and its
+        # gradient uses its own opposite face traces
+        return workloads.small_box_2d(n=1, seed=71, R=1, E=[4], order=2, mu=0.05)
+    if name == "empty_partition":
+        # member 1 owns no element: no stage has a ring from it
+        wl = workloads.small_box_2d(n=6, seed=72, R=2, E=[6, 3], order=3, mu=0.05)
+        wl.part = np.zeros_like(wl.part)
+        return wl
+    if name == "ragged_prefix":
+        # random partitions: prefixes and rings of every size, none a
+        # multiple of the elements per CTA
+        return workloads.small_box_2d(n=7, seed=73, R=3, E=[8, 6, 3], order=3, random_parts=True, mu=0.05)
+    raise KeyError(name)
+
+
+@pytest.mark.parametrize("precision", [pk.FP64, pk.MIXED])
+@pytest.mark.parametrize("name", ["one_element", "empty_partition", "ragged_prefix"])
+def test_viscous_edge_case_meshes(name, precision):
+    wl = _edge_case(name)
+    ref, rrec = oracle_run(wl, 4)
+    tested = 0
+    for variant in (0, 1):
+        for epb in (4, 8, 16):
+            s = pk.Solver(wl, pk.options(precision=precision, max_it=10, tol_r=1e-14, tol_g=1e-14))
+            pk.perrk_set_tuning(s.h, epb, 0, 128, variant)
+            try:
+                recs = [r[0] for r in s.step(4)]
+            except pk.PerrkError as err:
+                assert "invalid configuration" in str(err)      # a mapping whose shared memory does not fit
+                s.close()
+                continue
+            u = s.state()
+            s.close()
+            tested += 1
+            tol = gamma_explained_tol(recs, rrec, ref.U) if precision == pk.FP64 else TOL[precision]
+            assert rel_linf(u, ref.U) < tol, (name, variant, epb, rel_linf(u, ref.U), tol)
+    assert tested >= 2
