@@ -101,7 +101,7 @@ typedef struct {
     int volume_flux;              /* perrk_volume_flux */
     int surface_flux;             /* perrk_surface_flux */
     double mu;                    /* dynamic viscosity: 0 = Euler; > 0 adds the Navier-Stokes-Fourier viscous
-                                     terms (Euler 2D / 3D only), BR1 on entropy-variable gradients (Sec. 4.2) */
+                                     terms (Euler 2D / 3D only), BR1 on entropy-variable gradients (Sec. 4.3.2) */
     double prandtl;               /* Prandtl number Pr = c_p mu / kappa (> 0 when mu > 0), gas constant 1 */
 } perrk_scheme_desc;
 

@@ -131,7 +131,7 @@ def rhs(geo, phys, U):
 # ----------------------------------------------------------------------------
 # Parabolic part: BR1 (Bassi & Rebay 1997; Gassner, Winters, Hindenlang &
 # Kopriva 2018), the viscous discretisation of the paper's viscous test
-# (Sec. 4.2), with the gradients taken of the entropy variables.
+# (Sec. 4.3.2), with the gradients taken of the entropy variables.
 #
 # Gradient (one element, strong form, central trace W* = (W^- + W^+)/2):
 #   J_q q_l(q) = sum_k Ja^k_l(q) sum_m D_{qm} W(m along xi^k)

@@ -135,7 +135,7 @@ def euler_entropy_potential(u, n, gamma):
 
 def nsf_viscous_flux(u, gw, gamma, mu, prandtl):
     """Viscous flux of the compressible Navier-Stokes-Fourier equations (the
-    parabolic part of the paper's viscous test, Sec. 4.2: constant dynamic
+    parabolic part of the paper's viscous test, Sec. 4.3.2: constant dynamic
     viscosity mu, Stokes' hypothesis, Fourier heat conduction with Prandtl
     number Pr = c_p mu / kappa, c_p = gamma / (gamma - 1), gas constant 1 so
     T = p / rho).

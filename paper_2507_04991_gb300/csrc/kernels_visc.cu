@@ -1,5 +1,5 @@
 // Viscous terms of the compressible Navier-Stokes-Fourier equations (the
-// paper's viscous test, Sec. 4.2) by BR1 (Bassi & Rebay 1997) with the
+// paper's viscous test, Sec. 4.3.2) by BR1 (Bassi & Rebay 1997) with the
 // gradients taken of the entropy variables, for one P-ERK stage:
 //
 //   k_visc_flux  over the stage's gradient set (active prefix + the ring of

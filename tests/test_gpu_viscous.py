@@ -1,5 +1,5 @@
 """GPU parity of the Navier-Stokes-Fourier path (BR1 viscous terms on
-entropy-variable gradients, Sec. 4.2) against the oracle: the right-hand side
+entropy-variable gradients, Sec. 4.3.2) against the oracle: the right-hand side
 on box, curved and 3D meshes; the multirate stage loop with relaxation under
 random partition ids (the gradient set of a stage includes the inactive
 neighbours of the active elements); a batch of two instances; entropy decay

@@ -1,5 +1,5 @@
 """Pins of the oracle's Navier-Stokes-Fourier part (BR1 on entropy-variable
-gradients): the paper's traveling viscous shock (Sec. 4.2, eq.
+gradients): the paper's traveling viscous shock (Sec. 4.3.2, eq.
 ViscousShockSolution) as an exact solution of the full semidiscrete
 right-hand side, frame indifference and Stokes' hypothesis of the stress,
 polynomial exactness of the BR1 gradient and divergence, conservation, the
@@ -198,7 +198,7 @@ def _run(wl, p, E, dt, n, relax):
 def test_temporal_order_with_viscosity(p, E):
     """The relaxed multirate scheme keeps its order p on the Navier-Stokes-
     Fourier semidiscretisation (the paper's claim for entropy-diffusive
-    problems, Sec. 4.2), by self-convergence against a fine non-relaxed
+    problems, Sec. 4.3.2), by self-convergence against a fine non-relaxed
     fourth-order run to the relaxed run's own final time."""
     wl = workloads.small_box_2d(n=4, seed=8, R=2, E=E, order=p, mu=0.2)
     T = 0.4

@@ -197,7 +197,7 @@ def taylor_green(x, y, z, mach=0.1, gamma=GAMMA_GAS):
 
 
 def viscous_shock_prims(s, gamma=5.0 / 3.0, mu=0.15, rho0=1.0, vs=1.0):
-    """Traveling viscous shock of Sec. 4.2 (eq. ViscousShockSolution) at the
+    """Traveling viscous shock of Sec. 4.3.2 (eq. ViscousShockSolution) at the
     signed distance s = x0 along the shock normal (x0 = x - v t), for the
     Mach number Ma = 2 / sqrt(3 - gamma) at which the profile is explicit:
     c0 = v / Ma, p0 = c0^2 rho0 / gamma, chi = 2 exp(s / (2 l)),
@@ -386,7 +386,7 @@ def tgv_3d(n=64, n_fine=16, E=(8, 4), order=3, cfl=0.5, mu=0.0):
 
 
 def viscous_shock_2d(n=16, angle=0.0, L=2.0, gamma=5.0 / 3.0, mu=0.15, E=(4,), order=2):
-    """The viscous shock of Sec. 4.2 on the periodic square [-L, L]^2 of n x n
+    """The viscous shock of Sec. 4.3.2 on the periodic square [-L, L]^2 of n x n
     boxes, its normal rotated by `angle` in the plane (the state jumps across
     the periodic seams; away from them it is the traveling profile)."""
     e = np.linspace(-L, L, n + 1)
