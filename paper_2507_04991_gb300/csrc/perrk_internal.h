@@ -186,8 +186,8 @@ perrk_status launch_stage(Ctx &c, int stage, bool rhs_only, const double *in_u, 
                           float *out_kf, void *stream);
 perrk_status launch_convert(const double *src_d, float *dst_f, const float *src_f, double *dst_d, size_t n,
                             void *stream);
-// float64 <-> float pair (hi = round(x), lo = round(x - hi)); join: hi + lo
-perrk_status launch_split(const double *src, float *hi, float *lo, size_t n, void *stream);
+// float pair -> float64 (hi + lo); the split (hi = round(x), lo = round(x - hi))
+// is part of launch_split_entropy_set
 perrk_status launch_join(const float *hi, const float *lo, double *dst, size_t n, void *stream);
 perrk_status launch_relax_init(Ctx &c, void *stream);
 perrk_status launch_newton_pass(Ctx &c, void *stream);

@@ -31,25 +31,10 @@ perrk_status launch_convert(const double *src_d, float *dst_f, const float *src_
     return cuda_check((int)cudaGetLastError(), "convert launch");
 }
 
-__global__ void k_split(const double *src, float *hi, float *lo, size_t n) {
-    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const double x = src[i];
-    const float h = __double2float_rn(x);
-    hi[i] = h;
-    lo[i] = __double2float_rn(x - (double)h);
-}
-
 __global__ void k_join(const float *hi, const float *lo, double *dst, size_t n) {
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     dst[i] = (double)hi[i] + (double)lo[i];
-}
-
-perrk_status launch_split(const double *src, float *hi, float *lo, size_t n, void *stream) {
-    if (n == 0) return PERRK_OK;
-    k_split<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(src, hi, lo, n);
-    return cuda_check((int)cudaGetLastError(), "split launch");
 }
 
 perrk_status launch_join(const float *hi, const float *lo, double *dst, size_t n, void *stream) {
