@@ -23,9 +23,12 @@ p = 3 (b_1 = b_{S-1} = 1/6, b_S = 2/3, a_{S,S-1} = (1 - a_{S-1,S-2}) / 4):
 for a trial t = a_{S-1,S-2} the coefficients alpha_4 .. alpha_{E-1} fix the
 chain a_{S-2,S-3} .. a_{first+1,first} one at a time, and the last
 coefficient alpha_E is a scalar equation in t, solved by bracketing and
-bisection.  p = 4 keeps its default chain: its base stages (the constants of
-the fourth-order archetype) fix one coefficient, so the free set is not a
-linear family of polynomials.
+bisection.  p = 4: the base stages (the constants of the fourth-order
+archetype) fix one coefficient, so the polynomials a chain can reach are not
+a linear family; the chain entries a_{i,i-1} (rows first+1 .. S-3) are then
+optimised directly (optimised_family_p4): a least-squares fit to the
+linear-program optimum, refined by Nelder-Mead on the stable step, kept only
+where it beats the default chain.
 
 The spectrum of a context is taken from its own right-hand side through the
 C ABI (perrk_rhs), by finite differences column by column.
@@ -34,7 +37,8 @@ import math
 
 import numpy as np
 
-__all__ = ["optimal_polynomial", "stable_step", "member_chain", "optimised_tableau", "jacobian", "jacobian_spectrum"]
+__all__ = ["optimal_polynomial", "stable_step", "member_chain", "optimised_tableau", "optimised_family_p4",
+           "jacobian", "jacobian_spectrum"]
 
 
 def _cheb_values(x, deg):
@@ -221,7 +225,7 @@ def member_chain(p, c, S, E, alpha):
         # the root nearest the default a_{S-1,S-2} = 1/4
         t = min(roots, key=lambda r: abs(r - 0.25))
         return _chain_p3(c, S, E, alpha, t)[0]
-    raise NotImplementedError("p = 4 keeps its default chain")
+    raise NotImplementedError("p = 4: the chain is optimised directly (optimised_family_p4)")
 
 
 def optimised_tableau(p, E_list, alphas):
@@ -238,6 +242,70 @@ def optimised_tableau(p, E_list, alphas):
             asub[r, i - 1] = v
             a1[r, i - 1] = c[i - 1] - v
     return c, b, a1, asub
+
+
+def _full_matrix(c, a1, asub, r):
+    S = len(c)
+    A = np.zeros((S, S))
+    for i in range(1, S):
+        A[i, 0] += a1[r, i]
+        A[i, i - 1] += asub[r, i]
+    return A
+
+
+def _poly_of(b, A, E):
+    """alpha_0..alpha_E of the member (alpha_j = b^T A^{j-1} 1)."""
+    out = [1.0]
+    v = np.ones(len(b))
+    for _ in range(E):
+        out.append(float(b @ v))
+        v = A @ v
+    return np.array(out)
+
+
+def optimised_family_p4(spectrum, E_list, n_dir=32, max_eval=400):
+    """(c, b, a1, asub, steps) of a p = 4 family whose members' free chain
+    entries maximise the stable step on the spectrum; steps[r] is member r's
+    stable step (>= the default chain's)."""
+    from scipy.optimize import least_squares, minimize
+    from . import perrk_build_tableau
+    lam = _clean_spectrum(spectrum)
+    c, b, a1, asub = perrk_build_tableau(4, E_list)
+    S = len(c)
+    steps = []
+    for r, E in enumerate(E_list):
+        first = S - E + 2
+        rows = list(range(first + 1, S - 2))           # free rows (1-based); rows S-2 .. S are the base
+        a_def = np.array([asub[r, i - 1] for i in rows])
+
+        def set_chain(x):
+            for i, v in zip(rows, x):
+                asub[r, i - 1] = v
+                a1[r, i - 1] = c[i - 1] - v
+
+        def step_of(x, hi):
+            set_chain(x)
+            return stable_step(_poly_of(b, _full_matrix(c, a1, asub, r), E), lam, hi)
+
+        h_lp, alpha_lp = optimal_polynomial(lam, 4, E, n_dir=n_dir, rel_tol=1e-3)
+        h_def = step_of(a_def, 2.0 * h_lp)
+        best_x, best_h = a_def, h_def
+        if rows:
+            def fit(x):
+                set_chain(x)
+                al = _poly_of(b, _full_matrix(c, a1, asub, r), E)
+                return (al[5:] - alpha_lp[5:]) / np.abs(alpha_lp[5:]).clip(1e-300)
+            x0 = least_squares(fit, a_def, xtol=1e-14, ftol=1e-14).x
+            h0 = step_of(x0, 2.0 * h_lp)
+            if h0 > best_h:
+                best_x, best_h = x0, h0
+            res = minimize(lambda x: -step_of(x, 2.0 * h_lp), best_x, method="Nelder-Mead",
+                           options={"maxfev": max_eval, "xatol": 1e-8, "fatol": 1e-6 * best_h})
+            if -res.fun > best_h:
+                best_x, best_h = res.x, -res.fun
+        set_chain(best_x)
+        steps.append(best_h)
+    return c, b, a1, asub, steps
 
 
 def jacobian(solver, u=None, eps=1e-7):

@@ -96,33 +96,46 @@ def test_polynomial_family_step_parity(p, E):
     assert np.abs(u - ref.U).max() / np.abs(ref.U).max() < 1e-10
 
 
-def test_optimised_member_stable_where_default_grows():
-    """One partition, S = E = 8, p = 3, around a free stream (perturbation
-    1e-6, so the linearisation governs).  At the optimised step h_opt the
-    optimised member's amplification max |P(h lambda)| is <= 1 on the
-    spectrum the library's right-hand side gives, the default member's is
-    above 1; stepping for as many steps as that rate needs to grow 1e3-fold
-    shows the same on the GPU."""
+@pytest.mark.parametrize("p", [3, 4])
+def test_optimised_member_stable_where_default_grows(p):
+    """One partition, S = E = 8, around a free stream (perturbation 1e-6, so
+    the linearisation governs).  At the optimised step h_opt the optimised
+    member's amplification max |P(h lambda)| is <= 1 on the spectrum the
+    library's right-hand side gives, the default member's is above 1;
+    stepping for as many steps as that rate needs to grow 1e3-fold shows the
+    same on the GPU.  p = 3 from the optimised polynomial, p = 4 from its
+    directly optimised chain."""
     import math
-    S, p = 8, 3
+    S = 8
     wl = _one_partition(S, p)
     base = _free_stream(wl, 0.0, 0)
     s = pk.Solver(wl, pk.options(relaxation=False))
     lam = st.jacobian_spectrum(s, base)
     s.close()
-    h_opt, alpha = st.optimal_polynomial(lam, p, S, n_dir=32, rel_tol=1e-3)
+    if p == 3:
+        h_opt, _ = st.optimal_polynomial(lam, p, S, n_dir=32, rel_tol=1e-3)
+        _, alpha = st.optimal_polynomial(lam, p, S, n_dir=32, rel_tol=1e-3)
+        tab = st.optimised_tableau(p, [S], [alpha])
+    else:
+        c, b, a1, asub, steps = st.optimised_family_p4(lam, [S], max_eval=200)
+        tab, h_opt = (c, b, a1, asub), steps[0]
+    A = np.zeros((S, S))
+    for i in range(1, S):
+        A[i, 0] += tab[2][0, i]
+        A[i, i - 1] += tab[3][0, i]
+    alpha = T.stability_coeffs(tab[1], A)[:S + 1]
     a_def = T.stability_coeffs(T.weights(p, S), T.member(p, S, S))[:S + 1]
     h_def = st.stable_step(a_def, lam, 2.0 * h_opt)
-    assert h_opt > 2.0 * h_def, (h_opt, h_def)
+    assert h_opt > 1.5 * h_def, (h_opt, h_def)
     dt = h_opt
     rho_opt = np.abs(np.polyval(alpha[::-1], dt * lam)).max()
     rho_def = np.abs(np.polyval(a_def[::-1], dt * lam)).max()
-    assert rho_opt <= 1.0 + 1e-8 and rho_def > 1.0 + 1e-3, (rho_opt, rho_def)
+    assert rho_opt <= 1.0 + 1e-7 and rho_def > 1.0 + 1e-3, (rho_opt, rho_def)
     nsteps = min(5000, int(math.ceil(math.log(1e3) / math.log(rho_def))))
     u0 = _free_stream(wl, 1e-6, 2)
 
-    def growth(tab):
-        s = pk.Solver(wl, pk.options(relaxation=False), tableaux=[tab])
+    def growth(t):
+        s = pk.Solver(wl, pk.options(relaxation=False), tableaux=[t])
         s.set_state(u0)
         s.set_dt(dt)
         s.step(nsteps, info=False)
@@ -130,7 +143,7 @@ def test_optimised_member_stable_where_default_grows():
         s.close()
         return np.abs(u - base).max() / np.abs(u0 - base).max()
 
-    g_opt = growth(st.optimised_tableau(p, [S], [alpha]))
+    g_opt = growth(tab)
     g_def = growth(pk.perrk_build_tableau(p, [S]))
     assert g_opt < 20.0, (g_opt, nsteps)
     assert g_def > 100.0 or not np.isfinite(g_def), (g_def, nsteps, rho_def)

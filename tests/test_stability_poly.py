@@ -155,9 +155,28 @@ def test_gain_on_a_dg_spectrum():
     assert st.stable_step(alpha, lam, h) == h
 
 
+def test_p4_family_optimised_on_its_chain():
+    """p = 4: the chain entries are optimised directly.  The family keeps the
+    fourth-order conditions of every member pair (checked by the oracle on
+    the full Butcher matrices), each member is stable at its reported step,
+    and the member with free entries gains over the default chain."""
+    E_list = [7, 5]
+    c, b, a1, asub, steps = st.optimised_family_p4(SPEC, E_list, max_eval=150)
+    As = [_full(c, a1, asub, r) for r in range(len(E_list))]
+    worst, cons = T.order_residuals(c, b, As, 4)
+    assert worst < 1e-13 and cons < 1e-15
+    for r, E in enumerate(E_list):
+        al = T.stability_coeffs(b, As[r])[:E + 1]
+        assert np.abs(np.polyval(al[::-1], steps[r] * SPEC)).max() <= 1.0 + 1e-8
+        a_def = T.stability_coeffs(T.weights(4, max(E_list)), T.member(4, max(E_list), E))[:E + 1]
+        h_def = st.stable_step(a_def, SPEC, 3.0 * steps[r])
+        assert steps[r] >= h_def * (1.0 - 1e-12)
+    assert steps[0] > 1.1 * st.stable_step(T.stability_coeffs(T.weights(4, 7), T.member(4, 7, 7))[:8], SPEC, 10.0)
+
+
 def test_p4_chain_is_refused():
-    """p = 4's base stages fix one coefficient: no chain from an arbitrary
-    polynomial (the library keeps the default chain)."""
+    """p = 4's base stages fix one coefficient: no chain reproduces an
+    arbitrary polynomial (its chain is optimised directly instead)."""
     c = T.abscissae(4, 8)
     with pytest.raises(NotImplementedError):
         st.member_chain(4, c, 8, 8, np.ones(9))
