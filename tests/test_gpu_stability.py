@@ -113,8 +113,7 @@ def test_optimised_member_stable_where_default_grows(p):
     lam = st.jacobian_spectrum(s, base)
     s.close()
     if p == 3:
-        h_opt, _ = st.optimal_polynomial(lam, p, S, n_dir=32, rel_tol=1e-3)
-        _, alpha = st.optimal_polynomial(lam, p, S, n_dir=32, rel_tol=1e-3)
+        h_opt, alpha = st.optimal_polynomial(lam, p, S, n_dir=32, rel_tol=1e-3)
         tab = st.optimised_tableau(p, [S], [alpha])
     else:
         c, b, a1, asub, steps = st.optimised_family_p4(lam, [S], max_eval=200)
