@@ -34,6 +34,7 @@
 #ifndef PERRK_H
 #define PERRK_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus

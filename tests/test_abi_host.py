@@ -125,3 +125,24 @@ def test_newton_presets_accepted(lib, case):
         assert err.status == pk.PERRK_CUDA_ERROR or err.status == pk.PERRK_OUT_OF_MEMORY
         return
     pk.perrk_destroy(h)
+
+
+def test_header_compiles_as_c(tmp_path):
+    """include/perrk.h is a C header: it compiles as strict C11 and its
+    checkpoint records have the sizes the binding assumes."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "h.c"
+    src.write_text('#include "perrk.h"\n'
+                   'int main(void) {\n'
+                   '  _Static_assert(sizeof(perrk_checkpoint_header) == 40, "header");\n'
+                   '  _Static_assert(sizeof(perrk_resume_info) == 96, "resume");\n'
+                   '  return 0;\n}\n')
+    out = tmp_path / "h.o"
+    r = subprocess.run([cc, "-std=c11", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(ROOT, "include"),
+                        "-c", str(src), "-o", str(out)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    assert pk.C.sizeof(pk.perrk_checkpoint_header) == 40 and pk.C.sizeof(pk.perrk_resume_info) == 96
