@@ -12,7 +12,11 @@
  *     EntropyChange_EntropyVariables_ReArranged);
  *   - Newton solve of r(gamma) = H(U_n + gamma dt d) - H_n - gamma Delta H = 0
  *     (eq. RelaxationEquation, Sec. 3.1) and the relaxed update
- *     U_{n+1} = U_n + gamma dt d, t_{n+1} = t_n + gamma dt (eq. RRKM_Update).
+ *     U_{n+1} = U_n + gamma dt d, t_{n+1} = t_n + gamma dt (eq. RRKM_Update);
+ *   - optionally the Navier-Stokes-Fourier viscous terms in F (BR1 on
+ *     entropy-variable gradients, the paper's viscous test, Sec. 4.3.2);
+ *   - bisection and secant as alternatives to Newton (Sec. 3.1), checkpoint
+ *     and bit-identical resume.
  *
  * Conventions shared by all calls
  *   - polynomial degree N = 3 on Legendre-Gauss-Lobatto nodes; NP = 4^dim
