@@ -69,3 +69,23 @@ def test_vortex_error_against_exact():
         errs[prec] = float(np.abs(u - ex).max() / np.abs(ex).max())
     assert errs[pk.FP64] < 1e-2
     assert abs(errs[pk.MIXED] - errs[pk.FP64]) < 0.05 * errs[pk.FP64], errs
+
+
+def test_vortex_convergence_order():
+    """Observed order of the relaxed multirate scheme on the curved vortex
+    configuration (p = 3, N = 3, three partitions), refining space and time
+    together against the exact translating vortex (the paper's convergence
+    study design, Sec. 4.3.1)."""
+    T = 0.5
+    errs = []
+    for n in (24, 48, 96):
+        wl = workloads.vortex_2d(n=n)
+        nsteps = int(math.ceil(T / wl.dt))
+        wl.dt = T / nsteps
+        u, t = _run(wl, nsteps, pk.FP64)
+        inf = wl.info
+        ex = workloads.isentropic_vortex(wl.coords[:, :, 0], wl.coords[:, :, 1], t, inf["center"], inf["strength"],
+                                         L=inf["L"])
+        errs.append(float(np.abs(u - ex).max() / np.abs(ex).max()))
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert rates[-1] > 2.5 and errs[-1] < errs[0], (errs, rates)

@@ -29,9 +29,15 @@ def test_closed_form_gamma_quadratic_entropy():
         assert abs(rec.gamma - 1.0) > 100 * tol  # relaxation is active
 
 
+@pytest.mark.parametrize("assign", ["random", "round_robin"])
 @pytest.mark.parametrize("p,E", [(2, [6, 4, 2]), (3, [6, 4, 3]), (4, [8, 6, 5])])
-def test_linear_invariants_random_partitions(p, E):
+def test_linear_invariants_random_partitions(p, E, assign):
+    """Mass, momentum and energy to round-off whatever the partition ids:
+    random, or round-robin (neighbouring elements always in different
+    partitions), the paper's conservation experiments (Sec. 4.2)."""
     wl = workloads.small_box_2d(n=6, seed=3, R=3, E=E, order=p, random_parts=True)
+    if assign == "round_robin":
+        wl.part = (np.arange(wl.n_elem) % 3).astype(np.int32)
     s = perrk.Solver(wl)
     m0 = [s.geo.integrate(s.U[v]) for v in range(4)]
     for _ in range(6):
