@@ -418,7 +418,9 @@ def run_native(args):
                             tuning["stage_variant"])
         extra.set_mlp(W)
         ctxs.append(extra)
-    streams = [stream] + [torch.cuda.Stream(device=dev) for _ in range(n_ctx - 1)]
+    # side streams for every context (the current stream may be the legacy
+    # default stream, which would serialise with the others)
+    streams = [torch.cuda.Stream(device=dev) for _ in range(n_ctx)]
     for X in range(n_ctx):                                 # capture each context's graph outside the timing
         pk.perrk_set_state(ctxs[X].h, host_u.data_ptr(), on_device=pk.STATE_HOST_ASYNC, stream=streams[X].cuda_stream)
         pk.perrk_step(ctxs[X].h, 1, info=False, stream=streams[X].cuda_stream)
