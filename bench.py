@@ -163,9 +163,9 @@ def reduce_over_ranks(x, world, op):
 # launch (profiles/k_stage_batched2d_traffic.md).  It is reported only while
 # the stage kernel sources are the ones those captures measured.
 STAGE_TRAFFIC = {"workload": "batched2d",
-                 "bytes": {0: 1597573888 + 1228417792,      # generic kernel, 8 elements per CTA
-                           1: 1597730560 + 1228143104},     # box kernel, 8 elements per CTA
-                 "sources_sha256": "772268c2dd644df1b24463eccb6e35a36c4c688c32d62cb83920f13600d02f80"}
+                 "bytes": {0: 1597533952 + 1228019456,      # generic kernel, 8 elements per CTA
+                           1: 1597616640 + 1228039424},     # box kernel, 8 elements per CTA
+                 "sources_sha256": "31815bb2e126d71934589fa24e7e93251dd251af12e582f2c47e778234f3cd56"}
 STAGE_SOURCES = ["stage.cuh", "stage_box.cuh", "physics.cuh", "dfloat.cuh", "kernels_stage2d.cu", "stage_launch.cu"]
 
 
