@@ -240,6 +240,29 @@ def test_nonphysical_state_reported():
     s.close()
 
 
+@pytest.mark.parametrize("precision", [pk.FP64, pk.MIXED])
+def test_nonfinite_state_reported_and_context_recovers(precision):
+    """A NaN injected into a host copy of the state is reported as a
+    non-physical state (status and flags), and the context stays usable: a
+    good state stepped afterwards matches the oracle."""
+    wl = STEP_CASES["box_p3"]()
+    s = pk.Solver(wl, pk.options(precision=precision))
+    bad = wl.u0.copy()
+    bad[1, 7, 2] = np.nan
+    s.set_state(bad)
+    with pytest.raises(pk.PerrkError) as ei:
+        s.step(1)
+    assert ei.value.status == pk.PERRK_NONPHYSICAL_STATE
+    s.set_state(wl.u0)
+    recs = s.step(3)
+    u = s.state()
+    s.close()
+    assert all(r[0]["flags"] & (pk.FLAG_NONPHYSICAL | pk.FLAG_NONFINITE) == 0 for r in recs)
+    ref, rrec = oracle_run(wl, 3)
+    tol = gamma_explained_tol([r[0] for r in recs], rrec, ref.U) if precision == pk.FP64 else TOL[precision]
+    assert rel_linf(u, ref.U) < tol
+
+
 SOLVERS = {pk.SOLVER_BISECTION: "bisection", pk.SOLVER_SECANT: "secant"}
 
 
