@@ -19,8 +19,10 @@ Conventions (the input format of ``perrk_create``):
 
 Physical setups follow the paper's test cases: the isentropic vortex
 (Sec. 4.1.2, eqs. for rho, v, p of the vortex), the Kelvin-Helmholtz
-instability initial state (Sec. 3.2.2) and the Taylor-Green vortex (standard
-form, not in the paper).  Partition assignment uses the shortest element edge
+instability initial state (Sec. 3.2.2), the traveling viscous shock
+(Sec. 4.3.2, eq. ViscousShockSolution) and the Taylor-Green vortex (standard
+form, not in the paper).  A workload's ``mu`` > 0 (with ``prandtl``) asks for
+the Navier-Stokes-Fourier viscous terms.  Partition assignment uses the shortest element edge
 (Sec. 2.2, eq. CharSpeed_DG with h the minimal corner distance).
 """
 from __future__ import annotations
