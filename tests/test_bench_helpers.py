@@ -1,0 +1,43 @@
+"""Host-side helpers of bench.py (no GPU): the code digest that keeps a
+captured DRAM-traffic figure valid only while the kernel code is unchanged,
+and the bounded CPU-oracle samples."""
+import importlib.util
+import os
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _bench():
+    spec = importlib.util.spec_from_file_location("bench_module", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_code_digest_ignores_comments_not_code(tmp_path):
+    b = _bench()
+    a = tmp_path / "a.cu"
+    a.write_text("// header\n__global__ void k(float *x) {\n  x[0] = 1.0f; /* one */\n}\n")
+    ref = b.code_digest([str(a)])
+    a.write_text("// another header\n\n__global__ void k(float *x)  {\n\tx[0] = 1.0f;   // set\n}\n")
+    assert b.code_digest([str(a)]) == ref
+    a.write_text("__global__ void k(float *x) {\n  x[0] = 2.0f;\n}\n")
+    assert b.code_digest([str(a)]) != ref
+
+
+def test_stage_traffic_only_for_its_workload():
+    b = _bench()
+    assert b.stage_traffic("khi2d", 1) is None
+    assert b.stage_traffic("batched2d", 7) is None
+
+
+def test_cpu_samples_are_bounded():
+    """Single large instances are sampled at reduced resolution; batched
+    instances are sampled as they are."""
+    b = _bench()
+    import workloads
+    big = [workloads.tgv_3d(n=8, n_fine=2, mu=0.01)]
+    s, note = b.sample_instances("tgv3d_visc", big)
+    assert note and s[0].n_elem == 16 ** 3 and s[0].mu == big[0].mu
+    small = [workloads.small_box_2d(n=4)]
+    assert b.sample_instances("batched2d", small) == (small, None)
