@@ -320,7 +320,7 @@ perrk_status perrk_entropy_static(int equation, double gamma_gas, const double *
 /* One evaluation of F on all elements: u_in, k_out device arrays [V][n_elem][NP]. */
 perrk_status perrk_rhs(perrk_ctx *ctx, const double *u_in, double *k_out, void *stream);
 
-/* Learned Newton guess (spec form 4): a 2x64 tanh MLP on F = 6 features
+/* Learned Newton guess: a 2x64 tanh MLP on F = 6 features
  * available before the first Newton pass of step n, all from quantities the
  * step has already computed: (gamma_{n-1} - 1, gamma_{n-2} - 1, gamma_{n-3} - 1,
  * Delta H_n / A_n, (Delta H / A)_{n-1}, (Delta H / A)_{n-2}) with
