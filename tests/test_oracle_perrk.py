@@ -195,3 +195,36 @@ def test_root_finders_agree_euler():
     assert np.all(np.abs(g0 - 1.0) > 1e-9)
     for solver in (perrk.SOLVER_SECANT, perrk.SOLVER_BISECTION):
         assert np.max(np.abs(np.array(gammas[solver]) - g0)) < 1e-8, solver
+
+
+def test_update_matrix_row_sums_and_conservation():
+    """The fully discrete multirate update U_{n+1} = D U_n of a linear problem
+    (Sec. 3.2.1): rows of D sum to one and the omega J weighted sum is
+    conserved, for the unrelaxed step and for any gamma.  The linear operator
+    is the exact Jacobian (complex step) of the two-level Burgers DGSEM at
+    u = 1, i.e. linear advection; D comes from the oracle's partitioned stage
+    loop applied column by column."""
+    wl = workloads.burgers_1d()
+    s = perrk.Solver(wl)
+    n = wl.u0.size
+    one = np.ones_like(wl.u0)
+    L = np.empty((n, n))
+    h = 1e-30
+    for k in range(n):
+        e = np.zeros(n, complex)
+        e[k] = 1j * h
+        L[:, k] = s.rhs(one + e.reshape(one.shape)).ravel().imag / h
+    s.rhs = lambda U: (L @ U.ravel()).reshape(U.shape)
+    D1 = np.empty((n, n))
+    for k in range(n):
+        e = np.zeros(n)
+        e[k] = 1.0
+        d, _, _ = s.stages(e.reshape(one.shape), wl.dt)
+        D1[:, k] = e + wl.dt * d.ravel()
+    wJ = s.geo.wJ.ravel()
+    for gamma in (1.0, 0.97):
+        D = np.eye(n) + gamma * (D1 - np.eye(n))
+        assert np.abs(D.sum(axis=1) - 1.0).max() < 1e-12
+        assert np.abs(wJ @ D - wJ).max() < 1e-12 * np.abs(wJ).max()
+    # the multirate step is not the identity: the fine partition's stages act
+    assert np.abs(D1 - np.eye(n)).max() > 1e-3
