@@ -313,7 +313,10 @@ perrk_status perrk_stage_info(const perrk_ctx *ctx, int stage, int64_t *n_active
  * device current); make that first call before any stream capture.  All
  * calls share the array (it keeps the last call's contents; its counter is
  * cleared at the start of each call), so calls whose work overlaps on the
- * GPU race.  A non-physical node yields NaN in out[].  Asynchronous on stream. */
+ * GPU race.  A non-physical node (rho <= 0 or p <= 0) yields NaN in out[0]
+ * and out[1].  The cached array address is not refreshed after
+ * cudaDeviceReset: do not call this again on a device that was reset.
+ * Asynchronous on stream. */
 perrk_status perrk_entropy_static(int equation, double gamma_gas, const double *u, const double *wJ, long long n_nodes,
                                   double *out, void *stream);
 

@@ -8,6 +8,17 @@ forward:  x^ = (x - mean) / scale, h1 = tanh(W1 x^ + b1), h2 = tanh(W2 h1 + b2),
 loss:     mean over samples of (y - t)^2
 gradient: chain rule (d tanh(z)/dz = 1 - tanh(z)^2)
 Adam:     Kingma & Ba (2015) with beta1 = 0.9, beta2 = 0.999, eps = 1e-8.
+
+guess:    the learned Newton initial guess for the relaxation equation
+          (Sec. 3.1 starts Newton from gamma_{n-1}; the network predicts the
+          step-to-step change instead):
+          inc = clamp(out_scale * y(x), -tau, tau),
+          tau = 2 max(|g1 - g2|, |g2 - g3|) with g1, g2, g3 = gamma_{n-1},
+          gamma_{n-2}, gamma_{n-3} (the last converged values, 1 before the
+          first steps), and gamma_0 = g1 + inc; a guess that is not finite or
+          lies outside (0.5, 1.5) falls back to the method's own g1.  The clamp
+          is a trust region: the learned increment moves the guess no further
+          than the recent history of gamma itself moved.
 """
 import numpy as np
 
@@ -55,7 +66,8 @@ def loss_grad(w, X, T):
     return loss, g
 
 
-def adam(w, X, T, epochs, lr, b1=0.9, b2=0.999, eps=1e-8):
+def adam(w, X, T, epochs, lr, b1=0.9, b2=0.999, eps=1e-8, grads=None):
+    """Full-batch Adam; when grads is a list, each epoch's gradient is appended."""
     w = np.asarray(w, dtype=np.float64).copy()
     ntrain = sum(sizes()[:6])
     m = np.zeros(ntrain)
@@ -63,9 +75,28 @@ def adam(w, X, T, epochs, lr, b1=0.9, b2=0.999, eps=1e-8):
     for t in range(1, epochs + 1):
         _, g = loss_grad(w, X, T)
         g = g[:ntrain]
+        if grads is not None:
+            grads.append(g.copy())
         m = b1 * m + (1 - b1) * g
         v = b2 * v + (1 - b2) * g * g
         mh = m / (1 - b1 ** t)
         vh = v / (1 - b2 ** t)
         w[:ntrain] -= lr * mh / (np.sqrt(vh) + eps)
     return w
+
+
+def guess(w, x, g1, g2, g3):
+    """Learned initial guess gamma_0 for one step (see the module docstring).
+    x: the step's F features; g1, g2, g3: gamma_{n-1}, gamma_{n-2}, gamma_{n-3}."""
+    w = np.asarray(w, dtype=np.float64)
+    y, _ = forward(w, np.asarray(x, dtype=np.float64)[None, :])
+    out_scale = unpack(w)[8][0]
+    raw = out_scale * float(y[0])
+    if not np.isfinite(raw):
+        return g1
+    tau = 2.0 * max(abs(g1 - g2), abs(g2 - g3))
+    inc = min(max(raw, -tau), tau)
+    g0 = g1 + inc
+    if not np.isfinite(g0) or not abs(g0 - 1.0) < 0.5:
+        return g1
+    return g0

@@ -14,6 +14,8 @@
 // call.  Calls whose work overlaps on the GPU race on the scratch.
 #include <cuda_runtime.h>
 
+#include <atomic>
+#include <cmath>
 #include <cstdio>
 
 #include "physics.cuh"
@@ -50,13 +52,18 @@ __global__ void __launch_bounds__(kStaticThreads) k_entropy_static(const double 
         if constexpr (EQ == EQ_BURGERS) {
             sv = 0.5 * uv[0] * uv[0];
         } else {
-            euler_entropy<DIM>(uv, gam, sv, nullptr, bad);
+            uint32_t node_bad = 0;
+            euler_entropy<DIM>(uv, gam, sv, nullptr, node_bad);
+            // rho <= 0 or p <= 0: the entropy is undefined there (p = 0 alone
+            // would give +inf); report NaN in both sums
+            if (node_bad) sv = NAN;
+            bad |= node_bad;
         }
         const double w = __ldg(wJ + j);
         comp_add(s[0], c[0], w * sv);
         comp_add(s[1], c[1], w * fabs(sv));
     }
-    (void)bad;   // a non-physical node gives a NaN entropy, which reaches out[]
+    (void)bad;   // a non-physical node gives a NaN entropy, which reaches out[0] and out[1]
     __shared__ double sm[2 * 2 * 32];
     __shared__ int s_last;
     block_sum<2>(s, c, sm);
@@ -87,9 +94,14 @@ __global__ void __launch_bounds__(kStaticThreads) k_entropy_static(const double 
 }
 
 // Device address of the scratch array, looked up once per device (with that
-// device current) and cached.
+// device current) and cached.  The slots are atomic: two host threads making
+// their first call on one device at the same time both look the address up
+// (the same value) and store it, without a data race.  The cache is not
+// refreshed: after cudaDeviceReset the module, and with it the array, may
+// move, so a process that resets a device must not call this entry point on
+// it again.
 constexpr int kMaxDevices = 64;
-StaticScratch *g_scratch_addr[kMaxDevices] = {};
+std::atomic<StaticScratch *> g_scratch_addr[kMaxDevices] = {};
 
 perrk_status scratch_for_current_device(StaticScratch **out) {
     int dev = 0;
@@ -99,13 +111,15 @@ perrk_status scratch_for_current_device(StaticScratch **out) {
         set_error("entropy_static: device index beyond the supported range");
         return PERRK_NOT_SUPPORTED;
     }
-    if (!g_scratch_addr[dev]) {
+    StaticScratch *addr = g_scratch_addr[dev].load(std::memory_order_acquire);
+    if (!addr) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_static_scratch);
         if (e != cudaSuccess) return cuda_check((int)e, "entropy_static: cudaGetSymbolAddress");
-        g_scratch_addr[dev] = (StaticScratch *)p;
+        addr = (StaticScratch *)p;
+        g_scratch_addr[dev].store(addr, std::memory_order_release);
     }
-    *out = g_scratch_addr[dev];
+    *out = addr;
     return PERRK_OK;
 }
 

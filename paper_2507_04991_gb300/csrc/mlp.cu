@@ -50,9 +50,12 @@ __global__ void k_mlp_guess(const float *__restrict__ W, InstScalars *scal, int 
         // whose residual test is loose where r(gamma) is flat, to a distant
         // gamma); no history yet: the method's own guess
         const double tau = 2.0 * fmax(fabs(S.hist_gamma[0] - S.hist_gamma[1]), fabs(S.hist_gamma[1] - S.hist_gamma[2]));
-        const double inc = fmin(fmax((double)W[oOut] * (double)y, -tau), tau);
+        const double raw = (double)W[oOut] * (double)y;
+        // fmax / fmin drop a NaN operand, so a non-finite output is caught
+        // before the clamp: the guess stays gamma_{n-1}
+        const double inc = fmin(fmax(raw, -tau), tau);
         const double g0 = S.hist_gamma[0] + inc;
-        if (isfinite(g0) && fabs(g0 - 1.0) < 0.5) {
+        if (isfinite(raw) && isfinite(g0) && fabs(g0 - 1.0) < 0.5) {
             S.gamma = g0;
             S.gamma_guess = g0;
         }
