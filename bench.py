@@ -37,6 +37,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "DOF-stage updates/s per GB300, chosen vs plain FP64 form, at matched error"
+# what the chosen form computes in: FP32 flux differencing, surface fluxes and
+# stage registers K_i; the state U, the direction d and the entropy passes as
+# float pairs (hi + lo, ~48-bit significand) on the FP32 pipe; the Newton
+# scalars, Delta H and the step records in float64
+DTYPE_CHOSEN = "f32 fluxes/K + f32x2 (~48-bit) state, d, entropy + f64 scalars"
 UNIT = "DOF-stage updates/s"
 
 
@@ -160,9 +165,8 @@ def reduce_over_ranks(x, world, op):
 
 # DRAM traffic of the roofline kernel (all-active last stage of the batched 2D
 # workload) per stage kernel variant, from one ncu capture of each full-size
-# launch (profiles/k_stage_batched2d_traffic.md).  It is reported only while
-# the stage kernel sources are the ones those captures measured (code digest
-# without comments and whitespace).
+# launch.  It is reported only while the stage kernel sources are the ones
+# those captures measured (code digest without comments and whitespace).
 STAGE_TRAFFIC = {"workload": "batched2d",
                  "bytes": {0: 1597533952 + 1228019456,      # generic kernel, 8 elements per CTA
                            1: 1597616640 + 1228039424},     # box kernel, 8 elements per CTA
@@ -216,6 +220,79 @@ def sample_instances(name, insts):
     return insts, None
 
 
+def _oracle_worker(insts, barrier, cmds, results, widx):
+    """One host process of the all-cores oracle timing.  It builds the oracle
+    solvers of its instances (untimed), then for every command `window`
+    waits at a barrier shared by all processes and takes whole oracle steps
+    of its instances in turn until `window` seconds have passed; it reports
+    the DOF-stage updates of the completed steps and the time they took."""
+    from oracle import perrk as operrk
+    solvers = [(operrk.Solver(wl), wl) for wl in insts]
+    k = 0
+    while True:
+        window = cmds.get()
+        if window is None:
+            return
+        barrier.wait()
+        t0 = time.clock_gettime(time.CLOCK_MONOTONIC)
+        units, t1 = 0, t0
+        while t1 - t0 < window:
+            s, wl = solvers[k % len(solvers)]
+            s.step(wl.dt)
+            units += wl.dof_stage_per_step()
+            k += 1
+            t1 = time.clock_gettime(time.CLOCK_MONOTONIC)
+        results.put((widx, units, t1 - t0))
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+class OraclePool:
+    """The CPU oracle on all host cores: one spawned process per core (never
+    forked after CUDA use), one numpy thread each.  Process w owns instances
+    w, w + cores, ... of the first cores * per_core instances.  A round
+    starts every process at a barrier and runs for a fixed window; its
+    throughput is the sum over processes of completed DOF-stage updates over
+    their own busy time (all processes are busy for the whole window, so the
+    sum is the machine's aggregate rate, with the contention of all cores
+    running at once)."""
+
+    def __init__(self, insts, per_core, cores=None):
+        import multiprocessing as mp
+        self.cores = cores or host_cores()
+        n = self.cores * per_core
+        take = [insts[k % len(insts)] for k in range(n)]
+        self.n_inst = min(n, len(insts))
+        ctx = mp.get_context("spawn")
+        for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ[var] = "1"        # inherited at spawn
+        self.barrier = ctx.Barrier(self.cores)
+        self.results = ctx.Queue()
+        self.cmds = [ctx.Queue() for _ in range(self.cores)]
+        self.procs = [ctx.Process(target=_oracle_worker, args=(take[w::self.cores], self.barrier, self.cmds[w],
+                                                                self.results, w), daemon=True)
+                      for w in range(self.cores)]
+        for p in self.procs:
+            p.start()
+
+    def round(self, window):
+        for q in self.cmds:
+            q.put(window)
+        out = [self.results.get(timeout=900) for _ in self.procs]
+        return sum(u / t for _, u, t in out), max(t for _, _, t in out)
+
+    def close(self):
+        for q in self.cmds:
+            q.put(None)
+        for p in self.procs:
+            p.join(timeout=60)
+
+
 def oracle_sample(insts, seconds_cap):
     """Time the CPU oracle on a bounded sample: whole steps of the workload's
     instances in order until about seconds_cap of work."""
@@ -251,21 +328,42 @@ def run_reference(args):
         solvers[i].step(wl.dt)
         return wl.dof_stage_per_step(), time.perf_counter() - t0
 
-    for k in range(args.warmup):
-        one(k)
-    units, el = 0, 0.0
-    for k in range(args.steps):
-        u, t = one(args.warmup + k)
-        units += u
-        el += t
-    val = units / el
-    sample = (f"{args.steps} oracle steps, each of one instance in turn (numpy float64, one host thread), "
-              f"after {args.warmup} warm-up steps" + (f"; {s_note}" if s_note else ""))
+    cores = host_cores()
+    if args.ref_cores == 1 or cores == 1:
+        for k in range(args.warmup):
+            one(k)
+        units, el = 0, 0.0
+        for k in range(args.steps):
+            u, t = one(args.warmup + k)
+            units += u
+            el += t
+        val = units / el
+        used = 1
+        sample = (f"{args.steps} oracle steps, each of one instance in turn (numpy float64, one host thread), "
+                  f"after {args.warmup} warm-up steps" + (f"; {s_note}" if s_note else ""))
+    else:
+        # each timed step: a window of ref_window seconds in which every host
+        # core takes whole oracle steps of its own instances
+        pool = OraclePool(insts, 2, cores)
+        for _ in range(args.warmup):
+            pool.round(min(1.0, args.ref_window))
+        rates, el = [], 0.0
+        for _ in range(args.steps):
+            r, t = pool.round(args.ref_window)
+            rates.append(r)
+            el += t
+        pool.close()
+        val = float(np.mean(rates))
+        used = cores
+        sample = (f"{args.steps} timed windows of {args.ref_window:g} s, in each every one of {cores} host processes "
+                  f"(numpy float64, one thread each, started together at a barrier) takes whole oracle steps of its "
+                  f"own instances ({pool.n_inst} instances in all); after {args.warmup} warm-up windows"
+                  + (f"; {s_note}" if s_note else ""))
     line = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": f"{args.workload}: {desc}"},
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": used, "kind": "oracle", "sample": sample},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -438,7 +536,10 @@ def run_native(args):
         pk.perrk_set_state(ctxs[X].h, host_u.data_ptr(), on_device=pk.STATE_HOST_ASYNC, stream=streams[X].cuda_stream)
         pk.perrk_step(ctxs[X].h, 1, info=False, stream=streams[X].cuda_stream)
     torch.cuda.synchronize()
-    e2e_steps = max(2 * n_ctx, args.steps // 4)
+    # a fixed number of steps, independent of --steps: a short pipeline is
+    # mostly fill and drain (the first copy in and the last copy out overlap
+    # nothing)
+    e2e_steps = args.e2e_steps
     t0 = time.perf_counter()
     for k in range(e2e_steps):
         X = k % n_ctx
@@ -457,10 +558,17 @@ def run_native(args):
         return
     s_insts, s_note = sample_instances(args.workload, insts)
     cpu = oracle_sample(s_insts, args.cpu_seconds) if args.cpu_seconds > 0 else (None, 0, 0.0)
+    if args.cpu_per_core > 0:
+        pool = OraclePool(s_insts, args.cpu_per_core)
+        pool.round(1.0)                                   # warm-up window
+        cpu_all = (pool.round(args.cpu_window)[0], pool.cores, pool.n_inst, args.cpu_window)
+        pool.close()
+    else:
+        cpu_all = (None, 1, 0, 0.0)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32 fluxes + f64 state/relaxation", "data": "synthetic",
+        "vs_baseline": None, "dtype": DTYPE_CHOSEN, "data": "synthetic",
         "config": {"workload": f"{args.workload}: {desc}", "instances": len(insts), "dof": dof,
                    "dof_stage_per_step": dof_stage,
                    "form": "chosen: batched instances, FP32 flux differencing and surface fluxes, float64 state, "
@@ -481,9 +589,14 @@ def run_native(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": stage_traffic(args.workload, tuning["stage_variant"]), "kernel": f"k_stage (stage {S}, {st['n_active']} elements, all active)",
                      "algorithmic_bytes": st["bytes"], "kernel_ms": 1e3 * k_s, "peak_source": peak_src},
-        "cpu_baseline": {"value": cpu[0], "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"one oracle step each of the first {cpu[1]} instances ({cpu[2]:.1f} s, numpy float64, "
-                                   f"one thread)" + (f"; {s_note}" if s_note else "")},
+        "cpu_baseline": {"value": cpu_all[0], "unit": UNIT, "cores": cpu_all[1], "kind": "oracle",
+                         "sample": f"a {cpu_all[3]:g} s window in which each of {cpu_all[1]} host processes "
+                                   f"(numpy float64, one thread each, started together at a barrier) takes whole "
+                                   f"oracle steps of its own share of the first {cpu_all[2]} instances, after a 1 s "
+                                   f"warm-up window" + (f"; {s_note}" if s_note else ""),
+                         "one_core": {"value": cpu[0], "cores": 1,
+                                      "sample": f"one oracle step each of the first {cpu[1]} instances "
+                                                f"({cpu[2]:.1f} s, one thread)"}},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes,
                 "pipeline": f"{n_ctx} contexts, {n_ctx} streams, asynchronous pinned copies",
                 "results_agree": e2e_match},
@@ -503,7 +616,13 @@ def main():
     ap.add_argument("--workload", default="batched2d")
     ap.add_argument("--max-it", type=int, default=4)
     ap.add_argument("--train-steps", type=int, default=30)
-    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="bound of the one-thread oracle sample")
+    ap.add_argument("--cpu-per-core", type=int, default=2,
+                    help="instances per host process in the all-cores oracle sample (0: skip)")
+    ap.add_argument("--ref-cores", type=int, default=0, help="--impl reference: 1 = one thread, 0 = all host cores")
+    ap.add_argument("--e2e-steps", type=int, default=48, help="steps of the end-to-end pipeline (fixed)")
+    ap.add_argument("--cpu-window", type=float, default=6.0, help="seconds of the all-cores oracle window")
+    ap.add_argument("--ref-window", type=float, default=3.0, help="--impl reference: seconds per timed window")
     ap.add_argument("--mixed-tol-r", type=float, default=1e-12)
     ap.add_argument("--tuning", default=None,
                     help="EPB,GRID,VARIANT: pin the chosen form's stage mapping instead of autotuning it "

@@ -111,7 +111,16 @@ typedef struct {
 } perrk_scheme_desc;
 
 typedef struct {
-    int precision;                /* perrk_precision: FP64, or FP32 fluxes with float64 state/relaxation */
+    int precision;                /* perrk_precision.  PERRK_FP64: every node operation in float64.
+                                     PERRK_MIXED: flux differencing, surface fluxes and the stage
+                                     registers K_i in FP32; the state U and the direction d as float
+                                     pairs (hi + lo, ~48-bit significand), with the entropy passes,
+                                     the Newton residuals and the update evaluated in double-float on
+                                     the FP32 pipe; Delta H, the Newton scalars and the step records in
+                                     float64.  No float64 instruction runs per node.  Delta H then
+                                     carries the FP32 rounding of the K_i (noise of ~1e-7 relative to
+                                     its terms): EC runs in this form take PERRK_TARGET_PREV to keep
+                                     H_{n+1} = H_n to round-off. */
     int relaxation;               /* 1: P-ERRK (relaxed), 0: plain P-ERK (gamma = 1) */
     int newton_max_it;            /* maximum Newton passes per step (>= 0) */
     double newton_tol_r;          /* stop when |r| <= tol_r * sum omega J |s(U_n)| */

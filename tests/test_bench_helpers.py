@@ -41,3 +41,23 @@ def test_cpu_samples_are_bounded():
     assert note and s[0].n_elem == 16 ** 3 and s[0].mu == big[0].mu
     small = [workloads.small_box_2d(n=4)]
     assert b.sample_instances("batched2d", small) == (small, None)
+
+
+def test_all_cores_oracle_pool_runs_windows():
+    """The all-cores oracle timing: spawned processes, a barrier per window,
+    a positive aggregate rate from every process's completed steps."""
+    import sys
+    if ROOT not in sys.path:
+        sys.path.insert(0, ROOT)
+    import bench as b          # by name: the spawned processes import it the same way
+    import workloads
+    insts = [workloads.small_box_2d(n=4, seed=k) for k in range(3)]
+    pool = b.OraclePool(insts, per_core=1, cores=2)
+    try:
+        rate, busy = pool.round(0.2)
+        assert rate > 0 and busy >= 0.2
+        rate2, _ = pool.round(0.2)
+        assert rate2 > 0
+    finally:
+        pool.close()
+    assert all(not p.is_alive() for p in pool.procs)
