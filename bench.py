@@ -512,6 +512,12 @@ def run_native(args):
     k_s = timed(ranged("stage_all_active", lambda: pk.perrk_launch_stage(chosen.h, S - 1, stream=sh)), 20) / 20
     peak, peak_src = measured_peaks()
     achieved = st["bytes"] / k_s / 1e9
+    # the plain float64 form's all-active last stage, timed live (its per-node
+    # logarithms and divisions run on the FP64 pipe), and the FMA peaks of
+    # this GPU measured by the library's probe
+    st_p = pk.perrk_stage_info(plain.h, S - 1)
+    k_p = timed(ranged("plain_stage_all_active", lambda: pk.perrk_launch_stage(plain.h, S - 1, stream=sh)), 5) / 5
+    alu_peaks = {"fp32_tflops": pk.perrk_fma_peak(0, stream=sh), "fp64_tflops": pk.perrk_fma_peak(1, stream=sh)}
 
     # ---- end to end through the C ABI with host buffers (pinned): every step
     # copies its whole input state in and its whole result state out.  Three
@@ -578,6 +584,8 @@ def run_native(args):
                    "l2": ("inputs larger than L2; " if big_l2 else "") + "L2 flushed (256 MiB write) before every timed step",
                    "parallelism": f"replicas x{world}"},
         "plain_fp64": {"per_instance_loop": loop_value, "batched": plain_batched,
+                       "stage_all_active_ms": 1e3 * k_p, "stage_all_active_gbs": st_p["bytes"] / k_p / 1e9,
+                       "alu_peaks_measured": alu_peaks,
                        "ratio_chosen_vs_loop": (value / world / loop_value) if loop_value else None,
                        "ratio_chosen_vs_batched": value / world / plain_batched},
         "matched_error": {"chosen_vs_fp64_max_rel_linf_after_10_steps": rel,

@@ -364,6 +364,16 @@ perrk_status perrk_mlp_grad(const float *feats, const float *target, int n, cons
  * device arrays of n float64 values, x > 0.  Synchronises the stream. */
 perrk_status perrk_df_log(const double *x, double *y, int n, void *stream);
 
+/* Diagnostic (the paper has no counterpart): FMA throughput of the current
+ * device in TFLOP/s, FP32 (fp64 = 0) or FP64 (fp64 = 1), from independent FMA
+ * chains over 8 CTAs of 256 threads per SM, `iters` rounds of 8 chains per
+ * thread, timed with CUDA events on the stream (one FMA = 2 flops).  It is
+ * the peak against which kernels bound by plain ALU arithmetic (the float64
+ * form's stage and Newton kernels) are reported.  Allocates and frees a
+ * small output buffer; synchronises the stream.  INVALID_ARG for a null
+ * output or iters < 1. */
+perrk_status perrk_fma_peak(int fp64, int iters, double *tflops, void *stream);
+
 /* Last CUDA error string seen by this thread (static storage). */
 const char *perrk_last_error(void);
 const char *perrk_status_string(perrk_status s);

@@ -34,7 +34,7 @@ EXPORTED = [
     "perrk_shape", "perrk_set_state", "perrk_get_state", "perrk_set_dt", "perrk_step", "perrk_entropy",
     "perrk_rhs", "perrk_mlp_size", "perrk_mlp_features", "perrk_set_mlp", "perrk_mlp_train", "perrk_mlp_grad",
     "perrk_last_error", "perrk_status_string", "perrk_launch_stage", "perrk_stage_info", "perrk_df_log", "perrk_autotune", "perrk_tuning", "perrk_set_tuning", "perrk_entropy_static", "perrk_checkpoint_size",
-    "perrk_checkpoint_save", "perrk_checkpoint_load",
+    "perrk_checkpoint_save", "perrk_checkpoint_load", "perrk_fma_peak",
 ]
 
 
@@ -111,6 +111,7 @@ def load(path=LIB_PATH):
         "perrk_entropy_static": (I, [I, D, P, P, C.c_longlong, P, P]),
         "perrk_stage_info": (I, [P, I, P, P, P, P, P]),
         "perrk_status_string": (C.c_char_p, [I]),
+        "perrk_fma_peak": (I, [I, I, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -376,6 +377,13 @@ def perrk_entropy_static(equation, gamma_gas, u_ptr, wJ_ptr, n_nodes, out_ptr, s
     """Entropy functional without allocating: device pointers in and out."""
     _check(load().perrk_entropy_static(int(equation), float(gamma_gas), C.c_void_p(u_ptr), C.c_void_p(wJ_ptr),
                                        int(n_nodes), C.c_void_p(out_ptr), C.c_void_p(stream)), "perrk_entropy_static")
+
+
+def perrk_fma_peak(fp64, iters=4096, stream=0):
+    """Measured FMA throughput of the current device in TFLOP/s."""
+    t = C.c_double(0.0)
+    _check(load().perrk_fma_peak(int(bool(fp64)), int(iters), C.byref(t), C.c_void_p(stream)), "perrk_fma_peak")
+    return t.value
 
 
 def perrk_df_log(x_ptr, y_ptr, n, stream=0):
