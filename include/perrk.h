@@ -73,6 +73,7 @@ typedef enum { PERRK_SOLVER_NEWTON = 0, PERRK_SOLVER_BISECTION = 1, PERRK_SOLVER
 #define PERRK_FLAG_NEWTON_FALLBACK 0x1u   /* Newton did not converge: gamma = 1 taken (Sec. 3.2.1) */
 #define PERRK_FLAG_NONPHYSICAL     0x2u   /* rho <= 0 or p <= 0 met at some node */
 #define PERRK_FLAG_NONFINITE       0x4u   /* NaN / Inf met */
+#define PERRK_FLAG_TIMEOUT         0x8u   /* a bounded device wait gave up (the step's results are not valid) */
 
 /* Mesh (Sec. 2.2: elements carry a partition id r in 0..R-1). */
 typedef struct {
@@ -211,7 +212,9 @@ perrk_status perrk_get_state(perrk_ctx *ctx, double *u, int on_device, void *str
 perrk_status perrk_set_dt(perrk_ctx *ctx, int inst, double dt);
 
 /* Advance nsteps steps.  info: NULL (asynchronous) or host array of
- * nsteps * n_inst records (step-major), which forces a stream sync. */
+ * nsteps * n_inst records (step-major), which forces a stream sync; then
+ * PERRK_TIMEOUT if a bounded device wait gave up (PERRK_FLAG_TIMEOUT) and
+ * PERRK_NONPHYSICAL_STATE if a non-physical or non-finite value was met. */
 perrk_status perrk_step(perrk_ctx *ctx, int nsteps, perrk_step_info *info, void *stream);
 
 /* Checkpoint / resume.  A checkpoint is a host byte buffer holding everything
@@ -263,7 +266,8 @@ perrk_status perrk_checkpoint_load(perrk_ctx *ctx, const void *buf, size_t size,
  * mapping (one CTA per element group, or a persistent grid of k CTAs per SM)
  * and, for the mixed form on box elements, stage kernel variant (generic;
  * float4 box kernel; box kernel staging the next element group with
- * cp.async), then the relaxation block size; keeps the fastest and
+ * cp.async; in 2D the box kernel fed by a producer warp, two ways), then the
+ * relaxation block size; keeps the fastest and
  * re-captures the step graph.  Results do not depend on the choice (same
  * per-element arithmetic in the same order).  Overwrites the stage registers
  * and d (call between steps).  best_ms_out (nullable): mean time of the chosen
@@ -280,11 +284,25 @@ perrk_status perrk_tuning(const perrk_ctx *ctx, int *elems_per_cta, int *persist
  * on another run): elements per CTA (1D: 16, 32; 2D: 4, 8, 16; 3D: 1, 2, 4),
  * persistent grid size (0: one CTA per element group), relaxation block size
  * (128, 256), stage kernel variant (0/1/2 for the mixed form on box elements;
- * other contexts keep theirs).  Values outside these sets: PERRK_INVALID_ARG.
+ * 3 and 4 for the mixed form on 2D box elements: a producer warp stages
+ * each element group into a ring of shared-memory buffers while consumer
+ * warps compute, the own rows by bulk asynchronous copies (3) or by 16-byte
+ * cp.async (4), the neighbour face nodes by cp.async, with 4 or 8 elements
+ * per group and always a persistent grid, of the given size or, for 0, as
+ * many CTAs as are resident; other contexts keep theirs).  Values outside these sets:
+ * PERRK_INVALID_ARG.
  * A mapping whose shared memory does not fit is reported by the next launch
  * (PERRK_CUDA_ERROR, invalid configuration).  The step graph is re-captured. */
 perrk_status perrk_set_tuning(perrk_ctx *ctx, int elems_per_cta, int persistent_grid, int relax_threads,
                               int stage_variant);
+
+/* Test hook (the paper has no counterpart): with on != 0, the producer warp
+ * of stage kernel variants 3 and 4 fills no staging buffer, so that its consumer
+ * warps' bounded waits run out after about one second each; the next
+ * perrk_step with records then returns PERRK_TIMEOUT (PERRK_FLAG_TIMEOUT),
+ * with nothing left in flight on the GPU.  on = 0 restores normal launches;
+ * the context stays usable.  Other stage kernels ignore it. */
+perrk_status perrk_test_stall_producer(perrk_ctx *ctx, int on);
 
 /* H(U) = sum omega J s(U) of the current state per instance (host array [n_inst]); syncs. */
 perrk_status perrk_entropy(perrk_ctx *ctx, double *H, void *stream);

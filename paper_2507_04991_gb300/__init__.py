@@ -27,7 +27,7 @@ FP64, MIXED = 0, 1
 GUESS_ONE, GUESS_PREV, GUESS_MLP = 0, 1, 2
 TARGET_DELTA_H, TARGET_PREV, TARGET_INITIAL = 0, 1, 2
 SOLVER_NEWTON, SOLVER_BISECTION, SOLVER_SECANT = 0, 1, 2
-FLAG_NEWTON_FALLBACK, FLAG_NONPHYSICAL, FLAG_NONFINITE = 1, 2, 4
+FLAG_NEWTON_FALLBACK, FLAG_NONPHYSICAL, FLAG_NONFINITE, FLAG_TIMEOUT = 1, 2, 4, 8
 
 EXPORTED = [
     "perrk_default_options", "perrk_create", "perrk_create_batched", "perrk_destroy", "perrk_build_tableau",
@@ -35,6 +35,7 @@ EXPORTED = [
     "perrk_rhs", "perrk_mlp_size", "perrk_mlp_features", "perrk_set_mlp", "perrk_mlp_train", "perrk_mlp_grad",
     "perrk_last_error", "perrk_status_string", "perrk_launch_stage", "perrk_stage_info", "perrk_df_log", "perrk_autotune", "perrk_tuning", "perrk_set_tuning", "perrk_entropy_static", "perrk_checkpoint_size",
     "perrk_checkpoint_save", "perrk_checkpoint_load", "perrk_fma_peak",
+    "perrk_test_stall_producer",
 ]
 
 
@@ -112,6 +113,7 @@ def load(path=LIB_PATH):
         "perrk_stage_info": (I, [P, I, P, P, P, P, P]),
         "perrk_status_string": (C.c_char_p, [I]),
         "perrk_fma_peak": (I, [I, I, P, P]),
+        "perrk_test_stall_producer": (I, [P, I]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -377,6 +379,10 @@ def perrk_entropy_static(equation, gamma_gas, u_ptr, wJ_ptr, n_nodes, out_ptr, s
     """Entropy functional without allocating: device pointers in and out."""
     _check(load().perrk_entropy_static(int(equation), float(gamma_gas), C.c_void_p(u_ptr), C.c_void_p(wJ_ptr),
                                        int(n_nodes), C.c_void_p(out_ptr), C.c_void_p(stream)), "perrk_entropy_static")
+
+
+def perrk_test_stall_producer(h, on):
+    _check(load().perrk_test_stall_producer(h, int(bool(on))), "perrk_test_stall_producer")
 
 
 def perrk_fma_peak(fp64, iters=4096, stream=0):

@@ -23,6 +23,13 @@ struct perrk_ctx {
 
 namespace perrk {
 
+cudaError_t stage_ws_prepare_2d();
+
+// the mixed form on 2D axis-aligned box elements (stage kernel variants 0-3)
+static bool box2d(const Ctx &c) {
+    return c.opt.precision == PERRK_MIXED && c.equation != PERRK_BURGERS_1D && !c.curved && c.dim == 2;
+}
+
 static thread_local std::string g_err;
 
 void set_error(const std::string &e) { g_err = e; }
@@ -227,6 +234,8 @@ perrk_status perrk_create_batched(int n, const perrk_mesh_desc *mesh, const perr
     }
     st = alloc_ctx(h->c);
     if (st == PERRK_OK) st = cuda_check((int)cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking), "stream");
+    // the staged 2D box kernel's shared-memory opt-in, outside any capture
+    if (st == PERRK_OK && box2d(h->c)) st = cuda_check((int)stage_ws_prepare_2d(), "staged stage kernel set-up");
     if (st != PERRK_OK) {
         free_ctx(h->c);
         delete h;
@@ -482,6 +491,10 @@ perrk_status perrk_step(perrk_ctx *h, int nsteps, perrk_step_info *info, void *s
     if (info) {
         uint32_t fl = 0;
         PERRK_CUDA(cudaMemcpy(&fl, c.g_flags, sizeof fl, cudaMemcpyDeviceToHost), "flags read");
+        if (fl & PERRK_FLAG_TIMEOUT) {
+            set_error("a bounded device wait of the stage kernel gave up");
+            return PERRK_TIMEOUT;
+        }
         if (fl & (PERRK_FLAG_NONPHYSICAL | PERRK_FLAG_NONFINITE)) {
             set_error("non-physical or non-finite state met during the step");
             return PERRK_NONPHYSICAL_STATE;
@@ -505,7 +518,8 @@ perrk_status perrk_autotune(perrk_ctx *h, void *stream, float *best_ms_out) {
     PERRK_CUDA(cudaEventCreate(&e1), "event");
     // kernel variants: the mixed form on box elements has three stage kernels
     const bool box = c.opt.precision == PERRK_MIXED && c.equation != PERRK_BURGERS_1D && !c.curved && c.dim >= 2;
-    const std::vector<int> variants = box ? std::vector<int>{0, 1, 2} : std::vector<int>{c.stage_variant};
+    const std::vector<int> variants = box ? (c.dim == 2 ? std::vector<int>{0, 1, 2, 3, 4} : std::vector<int>{0, 1, 2})
+                                          : std::vector<int>{c.stage_variant};
     // timed launches: the first stage and the last (usually all elements active)
     const int stages[2] = {0, c.S - 1};
     float best = 1e30f;
@@ -589,8 +603,9 @@ perrk_status perrk_set_tuning(perrk_ctx *h, int elems_per_cta, int persistent_gr
                                    : (c.dim == 2 ? (elems_per_cta == 4 || elems_per_cta == 8 || elems_per_cta == 16)
                                                  : (elems_per_cta == 1 || elems_per_cta == 2 || elems_per_cta == 4));
     const bool box = c.opt.precision == PERRK_MIXED && c.equation != PERRK_BURGERS_1D && !c.curved && c.dim >= 2;
-    if (!epb_ok || persistent_grid < 0 || (relax_threads != 128 && relax_threads != 256) || stage_variant < 0 ||
-        stage_variant > 2 || (!box && stage_variant != 0 && stage_variant != c.stage_variant)) {
+    const bool ws_ok = stage_variant < 3 || (box && c.dim == 2 && (elems_per_cta == 4 || elems_per_cta == 8));
+    if (!epb_ok || !ws_ok || persistent_grid < 0 || (relax_threads != 128 && relax_threads != 256) ||
+        stage_variant < 0 || stage_variant > 4 || (!box && stage_variant != 0 && stage_variant != c.stage_variant)) {
         set_error("set_tuning: unsupported mapping for this context");
         return PERRK_INVALID_ARG;
     }
@@ -599,6 +614,13 @@ perrk_status perrk_set_tuning(perrk_ctx *h, int elems_per_cta, int persistent_gr
     c.relax_threads = relax_threads;
     c.stage_variant = box ? stage_variant : c.stage_variant;
     c.graph_dirty = true;
+    return PERRK_OK;
+}
+
+perrk_status perrk_test_stall_producer(perrk_ctx *h, int on) {
+    if (!h) return PERRK_INVALID_ARG;
+    h->c.ws_stall = on ? 1 : 0;
+    h->c.graph_dirty = true;
     return PERRK_OK;
 }
 

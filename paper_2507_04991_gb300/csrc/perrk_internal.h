@@ -162,7 +162,9 @@ struct Ctx {
     int stage_epb = 0;                        // elements per CTA in the stage kernel
     int stage_persistent = 0;                 // grid = min(groups, persistent blocks)
     int relax_threads = 128;
-    int stage_variant = 1;                    // mixed box: 0 generic kernel, 1 box kernel, 2 box kernel + cp.async staging
+    int stage_variant = 1;                    // mixed box: 0 generic kernel, 1 box kernel, 2 box kernel + cp.async staging,
+                                              // 3 (2D) box kernel fed by a producer warp
+    int ws_stall = 0;                         // test hook: the staged kernel's producer fills nothing
     bool tuned = false;
 
     // CUDA graph of one step

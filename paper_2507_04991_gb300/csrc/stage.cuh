@@ -56,6 +56,7 @@ struct StageParams {
     float Df[16];               // FP32 copies of the tables and constants (mixed form)
     float inv_w_f, gm1_f, inv_gm1_f, gam_f;
     uint32_t *flags;
+    int ws_stall;               // test hook of the staged 2D box kernel: its producer fills no buffer
 };
 
 // Geometry and constants in the kernel's arithmetic type, without per-use

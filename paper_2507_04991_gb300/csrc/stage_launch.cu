@@ -13,6 +13,7 @@ cudaError_t stage_launch_2d(const StageParams &, bool, bool, bool, int, int, cud
 cudaError_t stage_launch_3d(const StageParams &, bool, bool, bool, int, int, cudaStream_t);
 cudaError_t stage_launch_box_2d(const StageParams &, int, bool, int, cudaStream_t);
 cudaError_t stage_launch_box_3d(const StageParams &, int, bool, int, cudaStream_t);
+cudaError_t stage_launch_ws_2d(const StageParams &, int, bool, int, cudaStream_t);
 cudaError_t visc_launch(const StageParams &, int, bool, bool, cudaStream_t);
 
 int default_epb(int dim) { return dim == 1 ? 32 : (dim == 2 ? 8 : 2); }
@@ -96,6 +97,7 @@ perrk_status launch_stage(Ctx &c, int stage, bool rhs_only, const double *in_u, 
     P.wJ_f = c.g_wJ_f;
     P.box_tab = c.g_box_tab;
     P.flags = c.g_flags;
+    P.ws_stall = c.ws_stall;
     if (c.viscous) {
         P.ring = c.g_ring ? c.g_ring + (rhs_only ? 0 : c.ring_off[stage]) : nullptr;
         P.n_ring = rhs_only ? 0 : c.ring_off[stage + 1] - c.ring_off[stage];
@@ -122,7 +124,11 @@ perrk_status launch_stage(Ctx &c, int stage, bool rhs_only, const double *in_u, 
     }
     const bool burgers = c.equation == PERRK_BURGERS_1D;
     // mixed form on box elements: kernel variant 0 = the generic stage kernel,
-    // 1 = the float4 box kernel, 2 = the box kernel with cp.async staging
+    // 1 = the float4 box kernel, 2 = the box kernel with cp.async staging,
+    // 3 (2D) = the box kernel fed by a producer warp (own rows by bulk copies,
+    // neighbour face nodes by cp.async, into a ring of shared-memory buffers),
+    // 4 (2D) = the same with the own rows by 16-byte cp.async; their grid is
+    // persistent (stage_persistent CTAs, or as many as are resident)
     const bool box = mixed && !burgers && !c.curved && c.dim >= 2 && c.stage_variant > 0;
     if (box && !c.g_box_tab) {
         set_error("box stage kernel: node table missing");
@@ -139,7 +145,9 @@ perrk_status launch_stage(Ctx &c, int stage, bool rhs_only, const double *in_u, 
     int grid = groups;
     if (c.stage_persistent > 0) grid = std::min(groups, c.stage_persistent);
     cudaError_t e;
-    if (box && c.dim == 2) e = stage_launch_box_2d(P, epb, c.stage_variant == 2, grid, (cudaStream_t)stream);
+    if (box && c.dim == 2 && c.stage_variant >= 3)
+        e = stage_launch_ws_2d(P, epb, c.stage_variant == 3, c.stage_persistent, (cudaStream_t)stream);
+    else if (box && c.dim == 2) e = stage_launch_box_2d(P, epb, c.stage_variant == 2, grid, (cudaStream_t)stream);
     else if (box && c.dim == 3) e = stage_launch_box_3d(P, epb, c.stage_variant == 2, grid, (cudaStream_t)stream);
     else if (c.dim == 1) e = stage_launch_1d(P, burgers, mixed, c.curved, epb, grid, (cudaStream_t)stream);
     else if (c.dim == 2) e = stage_launch_2d(P, burgers, mixed, c.curved, epb, grid, (cudaStream_t)stream);
