@@ -26,13 +26,58 @@ import numpy as np
 from . import lgl as _lgl
 
 
+def lagrange_matrix(xn, s):
+    """L[i, j] = l_j(s_i): the Lagrange basis of the nodes xn evaluated at the
+    points s (barycentric form, extended precision)."""
+    xn = np.asarray(xn, dtype=np.longdouble)
+    s = np.asarray(s, dtype=np.longdouble)
+    n = len(xn)
+    lam = np.array([1 / np.prod([xn[j] - xn[k] for k in range(n) if k != j]) for j in range(n)])
+    L = np.zeros((len(s), n), dtype=np.longdouble)
+    for i, si in enumerate(s):
+        hit = np.nonzero(si == xn)[0]
+        if len(hit):
+            L[i, hit[0]] = 1
+            continue
+        t = lam / (si - xn)
+        L[i] = t / t.sum()
+    return L.astype(np.float64)
+
+
+def mortar_operators(N=3):
+    """Operators of the L2 projection mortar method (Kopriva 1996), the
+    non-conforming interface treatment the paper runs with its adaptive
+    meshes (Sec. 4.2 notes that it is not entropy-conservative).  A coarse
+    face s in [-1, 1] is split at s = 0 into two mortars m = 0 (lower half)
+    and m = 1 (upper half), each matching one fine face s' in [-1, 1] with
+    s = (s' - 1)/2 or (s' + 1)/2:
+      P[m][i, j] = l_j(s_m(x_i))      coarse face polynomial at the mortar's LGL nodes
+      R[m] = M^-1 P[m]^T M            L2 projection of a mortar polynomial back to the
+                                      coarse face, M_ij = int l_i l_j exact (Gauss-Legendre)
+    A flux g_m on each mortar (with the fine face's scaled normal) gives the
+    coarse face's flux G = R[0] g_0 + R[1] g_1 (with the coarse face's
+    normal: the factor 1/2 of ds = ds'/2 cancels the halved face length)."""
+    x, w, _ = _lgl.lgl(N)
+    gx, gw = np.polynomial.legendre.leggauss(N + 1)          # exact for degree 2N + 1
+    Lg = lagrange_matrix(x, gx)
+    M = Lg.T @ (gw[:, None] * Lg)
+    P = [lagrange_matrix(x, 0.5 * (x - 1.0)), lagrange_matrix(x, 0.5 * (x + 1.0))]
+    R = [np.linalg.solve(M, Pm.T @ M) for Pm in P]
+    return P, R
+
+
 class Geometry:
-    def __init__(self, coords, faces, N=3):
+    def __init__(self, coords, faces, N=3, mortars=None):
         self.coords = np.asarray(coords, dtype=np.float64)
         self.n_elem, self.NP, self.dim = self.coords.shape
         self.N = N
         self.x, self.w, self.D = _lgl.lgl(N)
         self.faces = np.asarray(faces)
+        # 2:1 non-conforming interfaces, rows (coarse element, its face, fine
+        # element on the lower half, fine element on the upper half)
+        self.mortars = np.zeros((0, 4), dtype=np.int64) if mortars is None else np.asarray(mortars, dtype=np.int64)
+        if len(self.mortars):
+            self.P_mortar, self.R_mortar = mortar_operators(N)
         self.shape_nodes = (N + 1,) * self.dim          # (k, j, i) order reversed below
         self._metrics()
 
@@ -122,10 +167,54 @@ def rhs(geo, phys, U):
         accm = np.moveaxis(acc, ax, -1)                # view
         np.add.at(accm[..., N], (slice(None), el), cL)
         np.add.at(accm[..., 0], (slice(None), er), cR)
+    if len(geo.mortars):
+        _mortar_terms(geo, phys, Ut, acc)
     K = -geo.flat(acc) / geo.J[None]
     if getattr(phys, "viscous", False):
+        if len(geo.mortars):
+            raise NotImplementedError("viscous terms on non-conforming meshes")
         K = K + viscous_rhs(geo, phys, U)
     return K
+
+
+def _mortar_terms(geo, phys, Ut, acc):
+    """Surface terms of the 2:1 mortars (see mortar_operators).  For each
+    mortar m the coarse face state is interpolated to the mortar nodes,
+    the numerical flux g_m = f*(U_plus, U_minus; nu_m) is evaluated with the
+    '+' side first and the fine face's scaled normal nu_m, the fine element
+    takes g_m like a conforming face, and the coarse element takes the L2
+    projection G = sum_m R[m] g_m (with its own normal in f(U_q).nu)."""
+    N = geo.N
+    P, R = geo.P_mortar, geo.R_mortar
+    ec, fc, elo, ehi = (geo.mortars[:, c] for c in range(4))
+    for f in range(2 * geo.dim):
+        sel = fc == f
+        if not np.any(sel):
+            continue
+        k, cplus = f >> 1, f & 1
+        ic, jf = (N, 0) if cplus else (0, N)           # coarse face index, fine face index along xi^k
+        ax = Ut.ndim - 1 - k
+        Uk = np.moveaxis(Ut, ax, -1)                   # [V, E, t, n]: face nodes t in tangential order
+        Jak = np.moveaxis(geo.tens(geo.Ja[k]), ax, -1)
+        accm = np.moveaxis(acc, ax, -1)
+        e_c = ec[sel]
+        uC = Uk[..., ic][:, e_c]                       # [V, nm, N+1]
+        nu_c = Jak[..., ic][:, e_c]
+        G = 0.0
+        for m, e_f in enumerate((elo[sel], ehi[sel])):
+            uF = Uk[..., jf][:, e_f]
+            nu_m = Jak[..., jf][:, e_f]
+            uCm = np.einsum("ij,vmj->vmi", P[m], uC)
+            g = phys.surface_flux(uCm, uF, nu_m) if cplus else phys.surface_flux(uF, uCm, nu_m)
+            G = G + np.einsum("ij,vmj->vmi", R[m], g)
+            if cplus:                                  # fine element on the '-' side
+                np.add.at(accm[..., jf], (slice(None), e_f), (-g + phys.flux(uF, nu_m)) / geo.w[0])
+            else:
+                np.add.at(accm[..., jf], (slice(None), e_f), (g - phys.flux(uF, nu_m)) / geo.w[N])
+        if cplus:
+            np.add.at(accm[..., ic], (slice(None), e_c), (G - phys.flux(uC, nu_c)) / geo.w[N])
+        else:
+            np.add.at(accm[..., ic], (slice(None), e_c), (-G + phys.flux(uC, nu_c)) / geo.w[0])
 
 
 # ----------------------------------------------------------------------------

@@ -75,7 +75,7 @@ class Solver:
         self.wl = wl
         self.phys = physics.Physics(wl.equation, wl.surface_flux, wl.gamma_gas, getattr(wl, "mu", 0.0),
                                     getattr(wl, "prandtl", 0.75))
-        self.geo = dgsem.Geometry(wl.coords, wl.faces)
+        self.geo = dgsem.Geometry(wl.coords, wl.faces, mortars=getattr(wl, "mortars", None))
         self.p = p or wl.order
         self.E = list(E or wl.E)
         if alphas is None:

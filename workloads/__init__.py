@@ -56,6 +56,9 @@ class Workload:
     info: dict = dataclasses.field(default_factory=dict)
     mu: float = 0.0          # dynamic viscosity (0: inviscid Euler)
     prandtl: float = 0.75    # Prandtl number of the viscous runs
+    # 2:1 non-conforming interfaces: rows (coarse element, its face, fine
+    # element on the face's lower half, fine element on the upper half)
+    mortars: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros((0, 4), dtype=np.int32))
 
     @property
     def n_elem(self):
@@ -459,6 +462,152 @@ def batched_2d(n_inst=256, seed=1, n_min=16, n_max=128, S=12, order=3):
         out.append(Workload(f"batch{k}_{ic}_{n}x{n}_R{R}", 2, "euler2d", coords, faces, part, list(E_by_R[R]), order,
                             to_soa(u0), dt, "ec_ranocha", "es_rusanov", info=dict(n=n, R=R, ic=ic)))
     return out
+
+
+# ------------------------------------------------------------- quadtree meshes
+
+class Quadtree:
+    """A 2:1-balanced quadtree of periodic square cells on [-L, L]^2 over an
+    n x n base grid.  A leaf is (level, ix, iy) with 0 <= ix, iy < n 2^level;
+    its cell is [-L + ix h, -L + (ix + 1) h] x [...], h = 2L / (n 2^level).
+    Mesh construction only: cell boxes, conforming face pairs, 2:1 mortars."""
+
+    def __init__(self, n, L, leaves):
+        self.n, self.L = n, L
+        self.leaves = sorted(set(leaves))
+        self._index = {c: i for i, c in enumerate(self.leaves)}
+
+    @classmethod
+    def uniform(cls, n, L):
+        return cls(n, L, [(0, ix, iy) for iy in range(n) for ix in range(n)])
+
+    def cells_at(self, lev):
+        return self.n << lev
+
+    def h(self, lev):
+        return 2.0 * self.L / self.cells_at(lev)
+
+    def centre(self, c):
+        lev, ix, iy = c
+        h = self.h(lev)
+        return -self.L + (ix + 0.5) * h, -self.L + (iy + 0.5) * h
+
+    def leaf_covering(self, lev, ix, iy):
+        """The leaf that contains cell (lev, ix, iy) (it or an ancestor), or None if that cell is refined."""
+        m = self.cells_at(lev)
+        ix, iy = ix % m, iy % m
+        for l in range(lev, -1, -1):
+            c = (l, ix >> (lev - l), iy >> (lev - l))
+            if c in self._index:
+                return c
+        return None
+
+    def refine(self, marks):
+        """Split the marked leaves into four children, then refine further
+        until every face neighbour differs by at most one level."""
+        leaves = set(self.leaves)
+        todo = [c for c in marks if c in leaves]
+        while todo:
+            for c in todo:
+                if c in leaves:
+                    leaves.remove(c)
+                    lev, ix, iy = c
+                    leaves.update((lev + 1, 2 * ix + a, 2 * iy + b) for a in (0, 1) for b in (0, 1))
+            tree = Quadtree(self.n, self.L, leaves)
+            todo = tree._unbalanced()
+        return Quadtree(self.n, self.L, leaves)
+
+    def coarsen(self, marks):
+        """Merge each family of four sibling leaves that are all marked into
+        their parent, unless that would break the 2:1 balance."""
+        leaves = set(self.leaves)
+        marked = set(marks)
+        parents = {(l - 1, ix >> 1, iy >> 1) for (l, ix, iy) in marked if l > 0}
+        for (l, px, py) in sorted(parents, reverse=True):
+            kids = [(l + 1, 2 * px + a, 2 * py + b) for a in (0, 1) for b in (0, 1)]
+            if not all(k in leaves and k in marked for k in kids):
+                continue
+            trial = (leaves - set(kids)) | {(l, px, py)}
+            if not Quadtree(self.n, self.L, trial)._unbalanced():
+                leaves = trial
+        return Quadtree(self.n, self.L, leaves)
+
+    def _unbalanced(self):
+        """Leaves with a face neighbour two or more levels finer (to be split)."""
+        out = set()
+        for c in self.leaves:
+            lev, ix, iy = c
+            for dx, dy in ((1, 0), (-1, 0), (0, 1), (0, -1)):
+                nb = self.leaf_covering(lev, ix + dx, iy + dy)
+                if nb is not None and nb[0] < lev - 1:
+                    out.add(nb)
+        return sorted(out)
+
+    def mesh(self):
+        """(coords [n_elem, 16, 2], faces [n_faces, 4], mortars [n_m, 4], level [n_elem])."""
+        t = 0.5 * (REF_NODES + 1.0)
+        ne = len(self.leaves)
+        coords = np.empty((ne, 16, 2))
+        q = np.arange(16)
+        for e, (lev, ix, iy) in enumerate(self.leaves):
+            h = self.h(lev)
+            coords[e, :, 0] = -self.L + (ix + t[q % 4]) * h
+            coords[e, :, 1] = -self.L + (iy + t[q // 4]) * h
+        faces, mortars = [], []
+        for e, (lev, ix, iy) in enumerate(self.leaves):
+            m = self.cells_at(lev)
+            # (face, neighbour cell offset, the two finer cells of a refined
+            # neighbour that touch this face: lower then upper half)
+            for f, (dx, dy) in enumerate(((-1, 0), (1, 0), (0, -1), (0, 1))):
+                nx, ny = (ix + dx) % m, (iy + dy) % m
+                nb = (lev, nx, ny)
+                if nb in self._index:
+                    if f & 1:
+                        faces.append((e, f, self._index[nb], f - 1))
+                    continue
+                if self.leaf_covering(lev, nx, ny) is not None:
+                    continue                            # coarser neighbour: its mortar row covers this face
+                if f < 2:
+                    col = 2 * nx + (1 if f == 0 else 0)   # the neighbour's column next to this face
+                    kids = [(lev + 1, col, 2 * ny), (lev + 1, col, 2 * ny + 1)]
+                else:
+                    row = 2 * ny + (1 if f == 2 else 0)
+                    kids = [(lev + 1, 2 * nx, row), (lev + 1, 2 * nx + 1, row)]
+                mortars.append((e, f, self._index[kids[0]], self._index[kids[1]]))
+        levels = np.array([c[0] for c in self.leaves])
+        return (coords, np.asarray(faces, dtype=np.int32).reshape(-1, 4),
+                np.asarray(mortars, dtype=np.int32).reshape(-1, 4), levels)
+
+
+def quadtree_workload(tree, name, E, order, ic="vortex", surface="es_rusanov", seed=0, cfl=0.3, levels_to_parts=None):
+    """Workload on a quadtree mesh: partition = refinement level (finest =
+    partition 0, Sec. 2.2: the stable step scales with the cell size),
+    initial state the translating isentropic vortex or the KHI state."""
+    coords, faces, mortars, levels = tree.mesh()
+    lmax = int(levels.max())
+    part = (lmax - levels).astype(np.int32) if levels_to_parts is None else np.asarray(levels_to_parts(levels), np.int32)
+    R = int(part.max()) + 1
+    rng = np.random.default_rng(BASE_SEED + 7 + seed)
+    x, y = coords[:, :, 0], coords[:, :, 1]
+    if ic == "vortex":
+        u0 = isentropic_vortex(x, y, 0.0, rng.uniform(-1, 1, 2), float(rng.uniform(3, 5)), L=tree.L, R=1.0)
+    else:
+        u0 = kelvin_helmholtz(x / tree.L, y / tree.L, phase=float(rng.uniform(0, 2 * math.pi)))
+    hmin = tree.h(lmax)
+    dt = cfl * hmin / (2 * N_POLY + 1) / 2.5
+    return Workload(name, 2, "euler2d", coords, faces, part, list(E[:R]), order, to_soa(u0), dt, "ec_ranocha", surface,
+                    info=dict(levels=levels, tree=tree), mortars=mortars)
+
+
+def quadtree_patch_2d(n=8, L=5.0, patch=0.35, depth=1, E=(6, 3), order=3, ic="vortex", surface="es_rusanov", seed=0):
+    """n x n base cells with the cells whose centre lies within patch * L of
+    the origin (in the max norm) refined `depth` times: 2:1 mortars around
+    each refined band."""
+    tree = Quadtree.uniform(n, L)
+    for _ in range(depth):
+        marks = [c for c in tree.leaves if max(abs(v) for v in tree.centre(c)) < patch * L]
+        tree = tree.refine(marks)
+    return quadtree_workload(tree, f"quadtree{n}_d{depth}", E, order, ic=ic, surface=surface, seed=seed)
 
 
 def by_name(name, **kw):
