@@ -81,9 +81,19 @@ typedef struct {
     int N;                        /* polynomial degree; must be 3 */
     int n_elem;
     const double *node_coords;    /* host, [n_elem][NP][dim]: physical LGL node positions */
-    int n_faces;                  /* must equal n_elem * dim (every element has one '+' face per direction) */
+    int n_faces;                  /* conforming interfaces; n_elem * dim when n_mortars = 0 */
     const int32_t *faces;         /* host, [n_faces][4] = (eL, fL, eR, fR) as above */
     const int32_t *partition_id;  /* host, [n_elem], values in 0..R-1 */
+    /* 2:1 non-conforming interfaces (2D meshes of axis-aligned boxes, inviscid):
+     * L2 projection mortars, the treatment of the paper's adaptive runs (Sec.
+     * 4.2 notes that they are not entropy-conservative).  Row (ec, fc, elo,
+     * ehi): face fc of the coarse element ec is split at its midpoint into
+     * two halves matched by face fc ^ 1 of the fine elements elo (the half at
+     * the face's lower tangential coordinate) and ehi; face nodes in the same
+     * tangential order on all three.  Every element face is then covered
+     * exactly once, by a conforming row or by a mortar row.  NULL / 0: none. */
+    int n_mortars;
+    const int32_t *mortars;       /* host, [n_mortars][4] */
 } perrk_mesh_desc;
 
 /* P-ERK family in low-storage form (Sec. 2.2, appendix A archetypes): the

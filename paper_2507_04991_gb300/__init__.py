@@ -41,7 +41,8 @@ EXPORTED = [
 
 class perrk_mesh_desc(C.Structure):
     _fields_ = [("dim", C.c_int), ("N", C.c_int), ("n_elem", C.c_int), ("node_coords", C.c_void_p),
-                ("n_faces", C.c_int), ("faces", C.c_void_p), ("partition_id", C.c_void_p)]
+                ("n_faces", C.c_int), ("faces", C.c_void_p), ("partition_id", C.c_void_p),
+                ("n_mortars", C.c_int), ("mortars", C.c_void_p)]
 
 
 class perrk_scheme_desc(C.Structure):
@@ -173,10 +174,11 @@ class _Keep:
         return _ptr(a)
 
 
-def mesh_desc(coords, faces, part, keep):
+def mesh_desc(coords, faces, part, keep, mortars=None):
     coords = np.ascontiguousarray(coords, dtype=np.float64)
     faces = np.ascontiguousarray(faces, dtype=np.int32)
     part = np.ascontiguousarray(part, dtype=np.int32)
+    mortars = np.zeros((0, 4), np.int32) if mortars is None else np.ascontiguousarray(mortars, dtype=np.int32)
     m = perrk_mesh_desc()
     m.dim = coords.shape[2]
     m.N = 3
@@ -185,6 +187,8 @@ def mesh_desc(coords, faces, part, keep):
     m.n_faces = faces.shape[0]
     m.faces = keep.add(faces)
     m.partition_id = keep.add(part)
+    m.n_mortars = mortars.shape[0]
+    m.mortars = keep.add(mortars) if mortars.shape[0] else None
     return m
 
 
@@ -549,7 +553,7 @@ class Solver:
         self.keep = _Keep()
         meshes, schemes = [], []
         for k, pb in enumerate(problems):
-            meshes.append(mesh_desc(pb.coords, pb.faces, pb.part, self.keep))
+            meshes.append(mesh_desc(pb.coords, pb.faces, pb.part, self.keep, getattr(pb, "mortars", None)))
             tab = tableaux[k] if tableaux else perrk_build_tableau(pb.order, pb.E)
             schemes.append(scheme_desc(pb.order, pb.E, *tab, EQUATION_CODES[pb.equation],
                                        SURFACE_CODES[pb.surface_flux], pb.gamma_gas, self.keep,

@@ -65,7 +65,7 @@ static void free_ctx(Ctx &c) {
                     c.g_elist, c.g_chunk_inst, c.g_chunk_e0, c.g_chunk_e1, c.g_inst_chunk0, c.g_inst_nchunks,
                     c.g_coef, c.g_coef_f, c.g_scal, c.g_partials, c.g_counters, c.g_flags, c.g_records, c.g_mlp,
                     c.g_dftab, c.g_node_f, c.g_elem_f, c.g_fnorm_f, c.g_wJ_f, c.g_ring, c.visc_fv,
-                    c.visc_kv};
+                    c.visc_kv, c.g_mortars, c.g_face_mortar, c.g_mtrace};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c.graph_exec) cudaGraphExecDestroy((cudaGraphExec_t)c.graph_exec);
@@ -128,6 +128,13 @@ static perrk_status alloc_ctx(Ctx &c) {
         PERRK_TRY(upload(c.g_wJ_lo, wlo, "weights"));
     }
     PERRK_TRY(upload(c.g_nbr, c.nbr, "neighbours"));
+    if (c.n_mortars > 0) {
+        PERRK_TRY(upload(c.g_mortars, c.mortars, "mortars"));
+        PERRK_TRY(upload(c.g_face_mortar, c.face_mortar, "mortars"));
+        const size_t nt = (size_t)3 * c.n_mortars * ipow4(c.dim - 1) * c.V * (mixed ? sizeof(float) : sizeof(double));
+        PERRK_CUDA(cudaMalloc(&c.g_mtrace, nt), "mortar traces");
+        PERRK_CUDA(cudaMemset(c.g_mtrace, 0, nt), "mortar traces");
+    }
     PERRK_TRY(upload(c.g_gp, c.gp_of_elem, "partitions"));
     PERRK_TRY(upload(c.g_elist, c.elist, "element list"));
     if (c.viscous) {
@@ -687,12 +694,20 @@ perrk_status perrk_stage_info(const perrk_ctx *h, int stage, int64_t *n_active, 
         }
         tot += (int64_t)na * (fvb + 2 * kvb + geo_v + 4 * (1 + NF));
     }
+    if (c.n_mortars > 0 && c.mortar_active[stage] > 0) {
+        // mortar kernel: the stage rows at the three elements' face nodes
+        // (U_n, K_1, K_{i-1}) and the traces of the three element faces written
+        const int64_t real = c.opt.precision == PERRK_MIXED ? 4 : 8;
+        const int64_t face = (int64_t)NFP * c.V * real;
+        tot += (int64_t)c.mortar_active[stage] * (3 * face * (stage > 0 ? 3 : 1) + 3 * face + 4 * 4);
+    }
     if (n_active) *n_active = na;
     if (bytes) *bytes = tot;
     if (n_stages) *n_stages = c.S;
     if (kernels_per_step) {
         int k = 0;
-        for (int i = 0; i < c.S; ++i) k += c.n_active[i] > 0 ? (c.viscous ? 3 : 1) : 0;
+        for (int i = 0; i < c.S; ++i)
+            k += (c.n_active[i] > 0 ? (c.viscous ? 3 : 1) : 0) + (c.n_mortars > 0 && c.mortar_active[i] > 0 ? 1 : 0);
         k += 2;  // relax_init + update
         if (c.opt.relaxation)
             k += c.opt.newton_max_it +

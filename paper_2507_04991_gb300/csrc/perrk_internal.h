@@ -125,7 +125,16 @@ struct Ctx {
     std::vector<double> geo_elem;             // box: [n_elem][8] = Ja_kk (dim) , invJ, J
     std::vector<double> fnorm;                // curved: [n_elem][4][4][2]; box: [n_elem][2 dim]
     std::vector<double> wJ;                   // [n_elem][NP] omega_q J_q (always)
-    std::vector<int32_t> nbr;                 // [n_elem][2 dim]
+    std::vector<int32_t> nbr;                 // [n_elem][2 dim] (a mortar face points to its own element)
+    // 2:1 mortars (2D boxes): rows (coarse, face, fine lower, fine upper) in
+    // global element ids, sorted by the largest E of their three elements
+    // (descending) so that each stage's mortars form a prefix; the trace
+    // slot of mortar m's element j (0 coarse, 1 lower, 2 upper) is 3 m + j
+    int n_mortars = 0;
+    std::vector<int32_t> mortars;             // [n_mortars][4]
+    std::vector<int32_t> face_mortar;         // [n_elem][2 dim]: trace slot or -1
+    std::vector<int32_t> mortar_active;       // [S] mortars to evaluate at each stage (prefix length)
+    double mortar_P[32] = {0}, mortar_R[32] = {0};   // interpolation to / projection from the two mortars
 
     // device buffers
     double *U = nullptr, *K1 = nullptr, *Ka = nullptr, *Kb = nullptr, *d = nullptr;
@@ -140,6 +149,9 @@ struct Ctx {
     float *g_node_f = nullptr, *g_elem_f = nullptr, *g_fnorm_f = nullptr, *g_wJ_f = nullptr;
     float *g_wJ_lo = nullptr;                 // mixed form: omega J = g_wJ_f + g_wJ_lo
     int32_t *g_nbr = nullptr, *g_gp = nullptr, *g_elist = nullptr, *g_ring = nullptr;
+    int32_t *g_mortars = nullptr, *g_face_mortar = nullptr;
+    void *g_mtrace = nullptr;                 // mortar traces [3 n_mortars][NFP][V], kernel precision: the
+                                              // numerical flux of each mortar element face (+ direction normal)
     void *visc_fv = nullptr;                  // viscous: node fluxes [dim][V-1][n_elem * NP] (kernel precision)
     void *visc_kv = nullptr;                  // viscous: + div f_v of the active elements [V-1][n_elem * NP]
     int32_t *g_chunk_inst = nullptr, *g_chunk_e0 = nullptr, *g_chunk_e1 = nullptr;
@@ -186,6 +198,7 @@ void df_tables(double gamma_gas, std::vector<float> &tab, std::vector<float> &co
 // in_u / in_uf into out_k / out_kf instead of the step buffers).
 perrk_status launch_stage(Ctx &c, int stage, bool rhs_only, const double *in_u, const float *in_uf, double *out_k,
                           float *out_kf, void *stream);
+perrk_status launch_mortars(Ctx &c, int stage, bool rhs_only, const double *in_u, const float *in_uf, void *stream);
 perrk_status launch_convert(const double *src_d, float *dst_f, const float *src_f, double *dst_d, size_t n,
                             void *stream);
 // float pair -> float64 (hi + lo); the split (hi = round(x), lo = round(x - hi))

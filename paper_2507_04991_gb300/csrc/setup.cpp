@@ -49,6 +49,66 @@ int min_E(int p) { return p == 2 ? 2 : (p == 3 ? 3 : 5); }
 int node_index(int dim, int i, int j, int k) { return i + 4 * j + (dim == 3 ? 16 * k : 0); }
 
 // Face node kk of face f: node index inside the element.
+// Lagrange basis of the LGL nodes x at the point s (extended precision).
+static void lagrange_at(const std::vector<double> &x, long double s, long double *l) {
+    const int n = (int)x.size();
+    for (int j = 0; j < n; ++j) {
+        long double v = 1.0L;
+        for (int k = 0; k < n; ++k)
+            if (k != j) v *= (s - (long double)x[k]) / ((long double)x[j] - (long double)x[k]);
+        l[j] = v;
+    }
+}
+
+// Operators of the L2 projection mortars (N = 3): P_m[j][i] = l_i((x_j -+ 1)/2)
+// and R_m = M^-1 P_m^T M with the exact mass matrix M_ij = int l_i l_j
+// (four-point Gauss-Legendre, exact for degree 7), index (m 4 + j) 4 + i.
+void mortar_operators(const std::vector<double> &x, double *P, double *R) {
+    const long double r = sqrtl(6.0L / 5.0L);
+    const long double gx[4] = {-sqrtl(3.0L / 7.0L + 2.0L / 7.0L * r), -sqrtl(3.0L / 7.0L - 2.0L / 7.0L * r),
+                               sqrtl(3.0L / 7.0L - 2.0L / 7.0L * r), sqrtl(3.0L / 7.0L + 2.0L / 7.0L * r)};
+    const long double s30 = sqrtl(30.0L);
+    const long double gw[4] = {(18.0L - s30) / 36.0L, (18.0L + s30) / 36.0L, (18.0L + s30) / 36.0L,
+                               (18.0L - s30) / 36.0L};
+    long double M[4][4] = {}, l[4];
+    for (int g = 0; g < 4; ++g) {
+        lagrange_at(x, gx[g], l);
+        for (int i = 0; i < 4; ++i)
+            for (int j = 0; j < 4; ++j) M[i][j] += gw[g] * l[i] * l[j];
+    }
+    // M^-1 by Gauss-Jordan elimination (M is symmetric positive definite)
+    long double A[4][8];
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 8; ++j) A[i][j] = j < 4 ? M[i][j] : (j - 4 == i ? 1.0L : 0.0L);
+    for (int c = 0; c < 4; ++c) {
+        const long double piv = A[c][c];
+        for (int j = 0; j < 8; ++j) A[c][j] /= piv;
+        for (int i = 0; i < 4; ++i)
+            if (i != c) {
+                const long double f = A[i][c];
+                for (int j = 0; j < 8; ++j) A[i][j] -= f * A[c][j];
+            }
+    }
+    for (int m = 0; m < 2; ++m) {
+        long double Pm[4][4];
+        for (int j = 0; j < 4; ++j) {
+            lagrange_at(x, 0.5L * ((long double)x[j] + (m ? 1.0L : -1.0L)), l);
+            for (int i = 0; i < 4; ++i) Pm[j][i] = l[i];
+        }
+        long double PtM[4][4] = {};
+        for (int i = 0; i < 4; ++i)
+            for (int j = 0; j < 4; ++j)
+                for (int k = 0; k < 4; ++k) PtM[i][j] += Pm[k][i] * M[k][j];
+        for (int i = 0; i < 4; ++i)
+            for (int j = 0; j < 4; ++j) {
+                long double v = 0.0L;
+                for (int k = 0; k < 4; ++k) v += A[i][4 + k] * PtM[k][j];
+                R[(m * 4 + i) * 4 + j] = (double)v;
+                P[(m * 4 + i) * 4 + j] = (double)Pm[i][j];
+            }
+    }
+}
+
 int face_node(int dim, int f, int kk) {
     int k = f / 2, s = f % 2, e = s ? 3 : 0;
     if (dim == 1) return e;
@@ -139,7 +199,10 @@ perrk_status build_ctx(Ctx &c, int n, const perrk_mesh_desc *mesh, const perrk_s
             return fail("instances must share dim, equation, fluxes, gamma_gas, viscosity and order");
         if (m.N != 3) return fail("only N = 3 is supported");
         if (m.n_elem <= 0 || !m.node_coords || !m.faces || !m.partition_id) return fail("empty mesh or null arrays");
-        if (m.n_faces != m.n_elem * dim) return fail("n_faces must equal n_elem * dim");
+        if (m.n_mortars < 0 || (m.n_mortars > 0 && !m.mortars)) return fail("n_mortars < 0 or null mortar rows");
+        if (m.n_mortars == 0 && m.n_faces != m.n_elem * dim) return fail("n_faces must equal n_elem * dim");
+        if (m.n_mortars > 0 && dim != 2) return fail("mortars (non-conforming faces) are supported in 2D only");
+        if (m.n_faces < 0) return fail("n_faces < 0");
         if (sc.order < 2 || sc.order > 4) return fail("order must be 2, 3 or 4");
         if (sc.R < 1 || sc.R > kMaxR) return fail("R out of range");
         if (sc.S < 2 || sc.S > 64) return fail("S out of range [2, 64]");
@@ -320,6 +383,60 @@ perrk_status build_ctx(Ctx &c, int n, const perrk_mesh_desc *mesh, const perrk_s
             c.nbr[gR * NF + fR] = (int32_t)gL;
         }
     }
+    // ---------------------------------------------------------- mortars
+    c.mortars.clear();
+    for (int k = 0; k < n; ++k) {
+        const perrk_mesh_desc &m = mesh[k];
+        if (m.n_mortars == 0) continue;
+        const Instance &I = c.inst[k];
+        if (!all_box) return fail("mortars need axis-aligned box elements");
+        if (c.viscous) return fail("viscous terms on non-conforming meshes are not supported");
+        std::vector<int> seen((size_t)m.n_elem * NF, 0);
+        for (int fi = 0; fi < m.n_faces; ++fi) {
+            const int32_t *row = m.faces + 4 * fi;
+            seen[(size_t)row[0] * NF + row[1]]++;
+            seen[(size_t)row[2] * NF + row[3]]++;
+        }
+        for (int mi = 0; mi < m.n_mortars; ++mi) {
+            const int32_t *row = m.mortars + 4 * mi;
+            const int ec = row[0], fc = row[1], el = row[2], eh = row[3];
+            if (ec < 0 || ec >= m.n_elem || el < 0 || el >= m.n_elem || eh < 0 || eh >= m.n_elem || fc < 0 ||
+                fc >= NF || el == eh || el == ec || eh == ec)
+                return fail("mortar row out of range");
+            const int ff = fc ^ 1;
+            if (seen[(size_t)ec * NF + fc]++ || seen[(size_t)el * NF + ff]++ || seen[(size_t)eh * NF + ff]++)
+                return fail("element face used twice");
+            // geometry: the fine faces are the two halves of the coarse face (up
+            // to a common translation for periodic pairs), in tangential order
+            const double *xc = m.node_coords + (size_t)ec * NP * dim;
+            const int qc0 = face_node(dim, fc, 0), qc3 = face_node(dim, fc, NFP - 1);
+            double sh[2] = {0, 0};
+            bool first = true;
+            for (int half = 0; half < 2; ++half) {
+                const double *xf = m.node_coords + (size_t)(half ? eh : el) * NP * dim;
+                for (int kk = 0; kk < NFP; ++kk) {
+                    const double sloc = 0.5 * (x[kk] + (half ? 1.0 : -1.0));   // coarse face coordinate
+                    const int qf = face_node(dim, ff, kk);
+                    for (int a = 0; a < dim; ++a) {
+                        const double want = 0.5 * (1.0 - sloc) * xc[qc0 * dim + a] + 0.5 * (1.0 + sloc) * xc[qc3 * dim + a];
+                        const double dd = xf[qf * dim + a] - want;
+                        if (first) sh[a] = dd;
+                        const double scl = 1.0 + std::fabs(want) + std::fabs(xf[qf * dim + a]);
+                        if (std::fabs(dd - sh[a]) > 1e-9 * scl) return fail("mortar faces are not the halves of the coarse face");
+                    }
+                    first = false;
+                }
+            }
+            const int32_t g[4] = {(int32_t)(I.elem0 + ec), fc, (int32_t)(I.elem0 + el), (int32_t)(I.elem0 + eh)};
+            c.mortars.insert(c.mortars.end(), g, g + 4);
+            c.nbr[(size_t)g[0] * NF + fc] = g[0];   // no conforming partner: the stage kernels read the trace
+            c.nbr[(size_t)g[2] * NF + ff] = g[2];
+            c.nbr[(size_t)g[3] * NF + ff] = g[3];
+        }
+    }
+    c.n_mortars = (int)(c.mortars.size() / 4);
+    if (c.n_mortars > 0) mortar_operators(x, c.mortar_P, c.mortar_R);
+
     // every face of every element needs a partner (interior or periodic): the
     // method has no boundary conditions here, and the kernels index nbr[] directly
     for (size_t i = 0; i < c.nbr.size(); ++i)
@@ -371,6 +488,13 @@ perrk_status build_ctx(Ctx &c, int n, const perrk_mesh_desc *mesh, const perrk_s
                 c.fnorm[e * NF + f] = v;
                 c.fnorm[nb * NF + (f - 1)] = v;
             }
+        // a mortar face has no conforming partner: its normal is the element's own
+        for (int mi = 0; mi < c.n_mortars; ++mi) {
+            const int32_t *r = &c.mortars[4 * mi];
+            const int fc = r[1];
+            c.fnorm[(size_t)r[0] * NF + fc] = c.geo_elem[(size_t)r[0] * 8 + fc / 2];
+            for (int h : {2, 3}) c.fnorm[(size_t)r[h] * NF + (fc ^ 1)] = c.geo_elem[(size_t)r[h] * 8 + fc / 2];
+        }
     }
 
     // ---------------------------------------------------------- ordering
@@ -387,6 +511,38 @@ perrk_status build_ctx(Ctx &c, int n, const perrk_mesh_desc *mesh, const perrk_s
             if (i == 1 || i >= S - E + 2) ++cnt;
         }
         c.n_active[i - 1] = cnt;
+    }
+    // mortars: sorted by the largest E of their elements, so that the mortars
+    // touching an active element form a prefix at every stage
+    c.face_mortar.assign(NE * NF, -1);
+    c.mortar_active.assign(S, 0);
+    if (c.n_mortars > 0) {
+        auto maxE = [&](int mi) {
+            int E = 0;
+            for (int j : {0, 2, 3}) E = std::max(E, c.E_of_gp[c.gp_of_elem[c.mortars[4 * mi + j]]]);
+            return E;
+        };
+        std::vector<int> ord(c.n_mortars);
+        std::iota(ord.begin(), ord.end(), 0);
+        std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return maxE(a) > maxE(b); });
+        std::vector<int32_t> sorted(c.mortars.size());
+        for (int i = 0; i < c.n_mortars; ++i)
+            for (int j = 0; j < 4; ++j) sorted[4 * i + j] = c.mortars[4 * ord[i] + j];
+        c.mortars.swap(sorted);
+        for (int mi = 0; mi < c.n_mortars; ++mi) {
+            const int32_t *r = &c.mortars[4 * mi];
+            c.face_mortar[(size_t)r[0] * NF + r[1]] = 3 * mi;
+            c.face_mortar[(size_t)r[2] * NF + (r[1] ^ 1)] = 3 * mi + 1;
+            c.face_mortar[(size_t)r[3] * NF + (r[1] ^ 1)] = 3 * mi + 2;
+        }
+        for (int i = 1; i <= S; ++i) {
+            int cnt = 0;
+            for (int mi = 0; mi < c.n_mortars; ++mi) {
+                const int E = maxE(mi);   // (the rows are already sorted)
+                if (i == 1 || i >= S - E + 2) ++cnt;
+            }
+            c.mortar_active[i - 1] = cnt;
+        }
     }
     // viscous runs: at each stage the inactive face neighbours of the active
     // prefix (a ring), whose BR1 gradients enter the active elements' viscous

@@ -57,6 +57,15 @@ struct StageParams {
     float inv_w_f, gm1_f, inv_gm1_f, gam_f;
     uint32_t *flags;
     int ws_stall;               // test hook of the staged 2D box kernel: its producer fills no buffer
+    // 2:1 mortars: rows (coarse, face, fine lower, fine upper) of this stage's
+    // n_mortar mortars, the trace slot of each element face (or -1; null
+    // without mortars), the traces [slot][NFP][V] in kernel precision and the
+    // operators P_m[j][i], R_m[j][i] (index (m NFP + j) NFP + i)
+    const int32_t *mortars, *face_mortar;
+    void *mtrace;
+    int n_mortar;
+    double mortar_P[32], mortar_R[32];
+    float mortar_Pf[32], mortar_Rf[32];
 };
 
 // Geometry and constants in the kernel's arithmetic type, without per-use
@@ -326,6 +335,14 @@ __global__ void __launch_bounds__(EPB * ipow4(DIM), stage_min_blocks<DIM, Real, 
                     if (DIM > 1) PERRK_AXIS_CASE(1)
                     if (DIM > 2) PERRK_AXIS_CASE(2)
 #undef PERRK_AXIS_CASE
+                }
+            }
+            if (P.face_mortar) {
+                // a 2:1 mortar face: the mortar kernel's flux for this element face
+                const int ms = P.face_mortar[(size_t)e * NF + f];
+                if (ms >= 0) {
+#pragma unroll
+                    for (int v = 0; v < V; ++v) fs[v] = static_cast<const Real *>(P.mtrace)[((size_t)ms * NFP + kk) * V + v];
                 }
             }
             const Real sg = self_plus ? Real(1) : Real(-1);

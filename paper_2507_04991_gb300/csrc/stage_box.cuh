@@ -458,6 +458,15 @@ __global__ void __launch_bounds__(EPB * ipow4(DIM), box_min_blocks<DIM, EPB, PIP
                         fs[v] -= 0.5f * lam * (uR - uL);
                     }
                 }
+                if (P.face_mortar) {
+                    // a 2:1 mortar face: the mortar kernel's flux for this element face
+                    const int ms = __ldg(P.face_mortar + (size_t)e * NF + f);
+                    if (ms >= 0) {
+#pragma unroll
+                        for (int v = 0; v < V; ++v)
+                            fs[v] = __ldg(static_cast<const float *>(P.mtrace) + ((size_t)ms * B::NFP + (sl % B::NFP)) * V + v);
+                    }
+                }
                 const float sc = self_plus ? inv_w : -inv_w;
 #pragma unroll
                 for (int v = 0; v < V; ++v) fs[v] *= sc;

@@ -15,6 +15,7 @@ cudaError_t stage_launch_box_2d(const StageParams &, int, bool, int, cudaStream_
 cudaError_t stage_launch_box_3d(const StageParams &, int, bool, int, cudaStream_t);
 cudaError_t stage_launch_ws_2d(const StageParams &, int, bool, int, cudaStream_t);
 cudaError_t visc_launch(const StageParams &, int, bool, bool, cudaStream_t);
+cudaError_t mortar_launch(const StageParams &, bool, cudaStream_t);
 
 int default_epb(int dim) { return dim == 1 ? 32 : (dim == 2 ? 8 : 2); }
 
@@ -98,6 +99,18 @@ perrk_status launch_stage(Ctx &c, int stage, bool rhs_only, const double *in_u, 
     P.box_tab = c.g_box_tab;
     P.flags = c.g_flags;
     P.ws_stall = c.ws_stall;
+    if (c.n_mortars > 0) {
+        P.mortars = c.g_mortars;
+        P.face_mortar = c.g_face_mortar;
+        P.mtrace = c.g_mtrace;
+        P.n_mortar = rhs_only ? c.n_mortars : c.mortar_active[stage];
+        for (int i = 0; i < 32; ++i) {
+            P.mortar_P[i] = c.mortar_P[i];
+            P.mortar_R[i] = c.mortar_R[i];
+            P.mortar_Pf[i] = (float)c.mortar_P[i];
+            P.mortar_Rf[i] = (float)c.mortar_R[i];
+        }
+    }
     if (c.viscous) {
         P.ring = c.g_ring ? c.g_ring + (rhs_only ? 0 : c.ring_off[stage]) : nullptr;
         P.n_ring = rhs_only ? 0 : c.ring_off[stage + 1] - c.ring_off[stage];
@@ -133,6 +146,15 @@ perrk_status launch_stage(Ctx &c, int stage, bool rhs_only, const double *in_u, 
     if (box && !c.g_box_tab) {
         set_error("box stage kernel: node table missing");
         return PERRK_INVALID_ARG;
+    }
+    if (c.n_mortars > 0) {
+        // the stage kernels that take mortar traces: the generic kernel and the box kernel (variant 1)
+        if (box && c.stage_variant >= 2) {
+            set_error("mortars: stage kernel variants 2-4 do not take mortar traces (use 0 or 1)");
+            return PERRK_NOT_SUPPORTED;
+        }
+        cudaError_t em = mortar_launch(P, mixed, (cudaStream_t)stream);
+        if (em != cudaSuccess) return cuda_check((int)em, "mortar launch");
     }
     if (c.viscous) {
         // viscous fluxes over the gradient set, their divergence over the

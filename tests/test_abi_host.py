@@ -146,3 +146,46 @@ def test_header_compiles_as_c(tmp_path):
                         "-c", str(src), "-o", str(out)], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
     assert pk.C.sizeof(pk.perrk_checkpoint_header) == 40 and pk.C.sizeof(pk.perrk_resume_info) == 96
+
+
+def _mortar_mesh():
+    wl = workloads.quadtree_patch_2d(n=8, depth=1, E=(6, 3), order=3)
+    keep = pk._Keep()
+    tab = pk.perrk_build_tableau(3, [6, 3])
+    return wl, keep, tab
+
+
+@pytest.mark.parametrize("breakage", ["swapped_halves", "face_twice", "missing_mortar", "index_range"])
+def test_invalid_mortars_rejected(lib, breakage):
+    """Malformed 2:1 mortar rows are refused before any device work."""
+    wl, keep, (c, b, a1, asub) = _mortar_mesh()
+    mortars = wl.mortars.copy()
+    faces = wl.faces
+    if breakage == "swapped_halves":
+        mortars[0, [2, 3]] = mortars[0, [3, 2]]
+    elif breakage == "face_twice":
+        mortars = np.concatenate([mortars, mortars[:1]])
+    elif breakage == "missing_mortar":
+        mortars = mortars[1:]
+    else:
+        mortars[0, 2] = wl.n_elem
+    m = pk.mesh_desc(wl.coords, faces, wl.part, keep, mortars)
+    s = pk.scheme_desc(3, [6, 3], c, b, a1, asub, pk.EULER_2D, pk.SURFACE_ES_RUSANOV, 1.4, keep)
+    with pytest.raises(pk.PerrkError) as ei:
+        pk.perrk_create(m, s, pk.options())
+    assert ei.value.status == pk.PERRK_INVALID_ARG, pk.last_error()
+    assert pk.last_error()
+
+
+def test_valid_mortar_mesh_passes_validation(lib):
+    """A well-formed quadtree mesh passes the host checks (without a GPU the
+    call then stops at the first device allocation)."""
+    wl, keep, (c, b, a1, asub) = _mortar_mesh()
+    m = pk.mesh_desc(wl.coords, wl.faces, wl.part, keep, wl.mortars)
+    s = pk.scheme_desc(3, [6, 3], c, b, a1, asub, pk.EULER_2D, pk.SURFACE_ES_RUSANOV, 1.4, keep)
+    try:
+        h = pk.perrk_create(m, s, pk.options())
+    except pk.PerrkError as err:
+        assert err.status in (pk.PERRK_CUDA_ERROR, pk.PERRK_OUT_OF_MEMORY), pk.last_error()
+        return
+    pk.perrk_destroy(h)
