@@ -467,18 +467,25 @@ def mlp_dataset(records):
     return np.asarray(X, dtype=np.float64), np.asarray(T, dtype=np.float64)
 
 
-def mlp_fit(X, T, epochs=400, lr=3e-3, seed=0, stream=0):
-    """Normalise the data, train on the device (perrk_mlp_train) and return
-    weights ready for perrk_set_mlp (normalisation folded into the layout)."""
+def mlp_fit(X, T, epochs=400, lr=3e-3, seed=0, stream=0, restarts=3):
+    """Normalise the data, train on the device (perrk_mlp_train) from
+    `restarts` random initialisations (seeds seed, seed + 1, ...), keep the
+    one with the lowest training loss (full-batch Adam on this small network
+    can stall in a poor fit from a single start) and return weights ready for
+    perrk_set_mlp (normalisation folded into the layout)."""
     mean = X.mean(axis=0)
     scale = X.std(axis=0)
     scale[scale == 0] = 1.0
     out_scale = float(np.abs(T).max()) or 1.0
-    W = mlp_init(seed)
     F, H = MLP_F, MLP_H
     Xn = ((X - mean) / scale).astype(np.float32)
     Tn = (T / out_scale).astype(np.float32)
-    W, loss = perrk_mlp_train(Xn, Tn, W, epochs, lr, stream)
+    best = None
+    for r in range(max(1, int(restarts))):
+        Wr, lr_loss = perrk_mlp_train(Xn, Tn, mlp_init(seed + r), epochs, lr, stream)
+        if best is None or lr_loss < best[1]:
+            best = (Wr, lr_loss)
+    W, loss = best
     W = W.copy()
     off = H * F + H + H * H + H + H + 1
     W[off:off + F] = mean

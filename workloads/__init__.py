@@ -532,6 +532,39 @@ class Quadtree:
                 leaves = trial
         return Quadtree(self.n, self.L, leaves)
 
+    def adapt(self, refine_marks, coarsen_marks):
+        """Coarsen the families whose four leaves are all in coarsen_marks
+        (where the 2:1 balance allows), then refine refine_marks (and
+        whatever the balance then requires).  Returns the new tree and the
+        map of its leaves to this tree's: rows (kind, a0, a1, a2, a3) with
+        kind 0 = the same leaf a0, 1 = child a1 (a + 2 b) of leaf a0,
+        2 = parent of leaves a0..a3 (child order a + 2 b)."""
+        refine_marks = set(refine_marks)
+        coarsen_marks = set(coarsen_marks) - refine_marks
+        families = {}
+        for (l, ix, iy) in coarsen_marks:
+            if l > 0:
+                families.setdefault((l - 1, ix >> 1, iy >> 1), []).append((l, ix, iy))
+        keep = set()
+        for par, kids in families.items():
+            sibs = [(par[0] + 1, 2 * par[1] + a, 2 * par[2] + b) for a in (0, 1) for b in (0, 1)]
+            if any(k in refine_marks for k in sibs):
+                keep.update(kids)
+        tree = self.coarsen(coarsen_marks - keep).refine(refine_marks)
+        old = self._index
+        rows = []
+        for (l, ix, iy) in tree.leaves:
+            if (l, ix, iy) in old:
+                rows.append((0, old[(l, ix, iy)], 0, 0, 0))
+            elif l > 0 and (l - 1, ix >> 1, iy >> 1) in old:
+                rows.append((1, old[(l - 1, ix >> 1, iy >> 1)], (ix & 1) + 2 * (iy & 1), 0, 0))
+            else:
+                kids = [(l + 1, 2 * ix + (c & 1), 2 * iy + (c >> 1)) for c in range(4)]
+                if not all(k in old for k in kids):
+                    raise ValueError("adapt changed a leaf by more than one level")
+                rows.append((2,) + tuple(old[k] for k in kids))
+        return tree, np.asarray(rows, dtype=np.int32)
+
     def _unbalanced(self):
         """Leaves with a face neighbour two or more levels finer (to be split)."""
         out = set()
@@ -597,6 +630,21 @@ def quadtree_workload(tree, name, E, order, ic="vortex", surface="es_rusanov", s
     dt = cfl * hmin / (2 * N_POLY + 1) / 2.5
     return Workload(name, 2, "euler2d", coords, faces, part, list(E[:R]), order, to_soa(u0), dt, "ec_ranocha", surface,
                     info=dict(levels=levels, tree=tree), mortars=mortars)
+
+
+def amr_marks(tree, alpha, thresholds=(0.01, 0.5), levels=(0, 1, 2)):
+    """Three-level controller: the target level of a leaf is levels[2] where
+    the indicator is at least thresholds[1], levels[1] where it is at least
+    thresholds[0], else levels[0]; leaves below their target are marked for
+    refinement, leaves above it for coarsening."""
+    ref, coa = [], []
+    for c, a in zip(tree.leaves, alpha):
+        target = levels[2] if a >= thresholds[1] else (levels[1] if a >= thresholds[0] else levels[0])
+        if c[0] < target:
+            ref.append(c)
+        elif c[0] > target:
+            coa.append(c)
+    return ref, coa
 
 
 def quadtree_patch_2d(n=8, L=5.0, patch=0.35, depth=1, E=(6, 3), order=3, ic="vortex", surface="es_rusanov", seed=0):
