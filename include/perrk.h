@@ -306,6 +306,35 @@ perrk_status perrk_tuning(const perrk_ctx *ctx, int *elems_per_cta, int *persist
 perrk_status perrk_set_tuning(perrk_ctx *ctx, int elems_per_cta, int persistent_grid, int relax_threads,
                               int stage_variant);
 
+/* Adaptive mesh refinement (the paper's adaptive runs, Sec. 3.2.2 and Sec.
+ * 5.3: refine where the shock-capturing indicator of Hennemann et al. on the
+ * density is large, change the mesh every few steps, re-derive the
+ * partitions from the element sizes, Sec. 2.2).  The mesh adaptation itself
+ * (a 2:1-balanced quadtree) is host logic of the caller (the Python
+ * package's amr module); these calls run its two device parts, for
+ * single-instance 2D Euler contexts on box elements, in float64 (the mixed
+ * form's state read as its float pair).
+ *
+ * perrk_amr_indicator: alpha (host, [n_elem]) = 1 / (1 + exp(-(s/T)(e - T)))
+ * per element, e the relative energy of the highest Legendre modes of the
+ * density (orthonormal basis; e = max((E_N - E_{N-1}) / E_N,
+ * (E_{N-1} - E_{N-2}) / E_{N-1}), E_k the energy of the modes up to degree k
+ * in each direction), T = 0.5 10^(-1.8 (N+1)^(1/4)), s = log((1-1e-4)/1e-4).
+ * Synchronises the stream.
+ *
+ * perrk_amr_transfer: the state of src carried to the context dst of the
+ * adapted mesh.  map (host, [dst n_elem][5]) row (kind, a0, a1, a2, a3):
+ * kind 0 = dst element is src element a0; 1 = child a1 (a + 2 b: a the half
+ * in xi, b in eta) of src element a0, by interpolation of the parent
+ * polynomial; 2 = parent of src elements a0..a3 (child order a + 2 b), by L2
+ * projection.  Element integrals sum omega J u are kept up to rounding.  dst
+ * then holds the new state as after perrk_set_state, except that the time,
+ * the relaxation history (gamma and Delta H / A of the last steps) and the
+ * step count carry over from src.  INVALID_ARG for map rows out of range.
+ * Synchronises the stream. */
+perrk_status perrk_amr_indicator(perrk_ctx *ctx, double *alpha, void *stream);
+perrk_status perrk_amr_transfer(const perrk_ctx *src, perrk_ctx *dst, const int32_t *map, void *stream);
+
 /* Test hook (the paper has no counterpart): with on != 0, the producer warp
  * of stage kernel variants 3 and 4 fills no staging buffer, so that its consumer
  * warps' bounded waits run out after about one second each; the next

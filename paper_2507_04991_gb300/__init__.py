@@ -35,7 +35,7 @@ EXPORTED = [
     "perrk_rhs", "perrk_mlp_size", "perrk_mlp_features", "perrk_set_mlp", "perrk_mlp_train", "perrk_mlp_grad",
     "perrk_last_error", "perrk_status_string", "perrk_launch_stage", "perrk_stage_info", "perrk_df_log", "perrk_autotune", "perrk_tuning", "perrk_set_tuning", "perrk_entropy_static", "perrk_checkpoint_size",
     "perrk_checkpoint_save", "perrk_checkpoint_load", "perrk_fma_peak",
-    "perrk_test_stall_producer",
+    "perrk_test_stall_producer", "perrk_amr_indicator", "perrk_amr_transfer",
 ]
 
 
@@ -115,6 +115,8 @@ def load(path=LIB_PATH):
         "perrk_status_string": (C.c_char_p, [I]),
         "perrk_fma_peak": (I, [I, I, P, P]),
         "perrk_test_stall_producer": (I, [P, I]),
+        "perrk_amr_indicator": (I, [P, P, P]),
+        "perrk_amr_transfer": (I, [P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -383,6 +385,21 @@ def perrk_entropy_static(equation, gamma_gas, u_ptr, wJ_ptr, n_nodes, out_ptr, s
     """Entropy functional without allocating: device pointers in and out."""
     _check(load().perrk_entropy_static(int(equation), float(gamma_gas), C.c_void_p(u_ptr), C.c_void_p(wJ_ptr),
                                        int(n_nodes), C.c_void_p(out_ptr), C.c_void_p(stream)), "perrk_entropy_static")
+
+
+def perrk_amr_indicator(h, stream=0):
+    """Refinement indicator per element (host float64 array)."""
+    n_elem = perrk_shape(h)[0]
+    a = np.zeros(n_elem)
+    _check(load().perrk_amr_indicator(h, _ptr(a), C.c_void_p(stream)), "perrk_amr_indicator")
+    return a
+
+
+def perrk_amr_transfer(src, dst, amap, stream=0):
+    m = np.ascontiguousarray(amap, dtype=np.int32)
+    if m.ndim != 2 or m.shape[1] != 5 or m.shape[0] != perrk_shape(dst)[0]:
+        raise ValueError("map must be [n_elem of dst][5]")
+    _check(load().perrk_amr_transfer(src, dst, _ptr(m), C.c_void_p(stream)), "perrk_amr_transfer")
 
 
 def perrk_test_stall_producer(h, on):

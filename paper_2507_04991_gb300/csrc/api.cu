@@ -624,6 +624,73 @@ perrk_status perrk_set_tuning(perrk_ctx *h, int elems_per_cta, int persistent_gr
     return PERRK_OK;
 }
 
+static bool amr_ok(const Ctx &c) {
+    return c.dim == 2 && !c.curved && c.equation == PERRK_EULER_2D && c.n_inst == 1;
+}
+
+perrk_status perrk_amr_indicator(perrk_ctx *h, double *alpha, void *stream) {
+    if (!h || !alpha) return PERRK_INVALID_ARG;
+    Ctx &c = h->c;
+    if (!amr_ok(c)) {
+        set_error("amr_indicator: single-instance 2D Euler contexts on box elements only");
+        return PERRK_NOT_SUPPORTED;
+    }
+    std::vector<double> x, w, D;
+    lgl_tables(x, w, D);
+    AmrIndicatorConsts K;
+    amr_indicator_consts(x, K);
+    cudaStream_t st = (cudaStream_t)stream;
+    double *dev = nullptr;
+    PERRK_CUDA(cudaMalloc((void **)&dev, (size_t)c.n_elem * sizeof(double)), "amr indicator alloc");
+    perrk_status s = launch_amr_indicator(c, K, dev, st);
+    if (s == PERRK_OK)
+        s = cuda_check((int)cudaMemcpyAsync(alpha, dev, (size_t)c.n_elem * sizeof(double), cudaMemcpyDeviceToHost, st),
+                       "amr indicator copy");
+    if (s == PERRK_OK) s = cuda_check((int)cudaStreamSynchronize(st), "amr indicator sync");
+    cudaFree(dev);
+    return s;
+}
+
+perrk_status perrk_amr_transfer(const perrk_ctx *hs, perrk_ctx *hd, const int32_t *map, void *stream) {
+    if (!hs || !hd || !map || hs == hd) return PERRK_INVALID_ARG;
+    const Ctx &a = hs->c;
+    Ctx &b = hd->c;
+    if (!amr_ok(a) || !amr_ok(b) || a.V != b.V) {
+        set_error("amr_transfer: single-instance 2D Euler contexts on box elements only");
+        return PERRK_NOT_SUPPORTED;
+    }
+    for (int e = 0; e < b.n_elem; ++e) {
+        const int32_t *r = map + 5 * (size_t)e;
+        const int kind = r[0];
+        bool ok = kind >= 0 && kind <= 2 && r[1] >= 0 && r[1] < a.n_elem;
+        if (kind == 1) ok = ok && r[2] >= 0 && r[2] < 4;
+        if (kind == 2)
+            for (int k = 2; k <= 4; ++k) ok = ok && r[k] >= 0 && r[k] < a.n_elem;
+        if (!ok) {
+            set_error("amr_transfer: map row out of range");
+            return PERRK_INVALID_ARG;
+        }
+    }
+    std::vector<double> x, w, D;
+    lgl_tables(x, w, D);
+    AmrOps O;
+    mortar_operators(x, O.P, O.R);
+    cudaStream_t st = (cudaStream_t)stream;
+    int32_t *dmap = nullptr;
+    const size_t mb = (size_t)b.n_elem * 5 * sizeof(int32_t);
+    PERRK_CUDA(cudaMalloc((void **)&dmap, mb), "amr map alloc");
+    perrk_status s = cuda_check((int)cudaMemcpyAsync(dmap, map, mb, cudaMemcpyHostToDevice, st), "amr map copy");
+    if (s == PERRK_OK) s = launch_amr_transfer(a, b, dmap, O, st);
+    if (s == PERRK_OK) s = cuda_check((int)cudaMemsetAsync(b.g_flags, 0, sizeof(uint32_t), st), "flags clear");
+    // the new state's entropy scalars (and, mixed form, its float pair), as set_state would
+    if (s == PERRK_OK) s = b.Uf ? launch_split_entropy_set(b, st) : launch_entropy_set(b, st);
+    if (s == PERRK_OK) s = launch_amr_history(a, b, st);
+    if (s == PERRK_OK) s = cuda_check((int)cudaStreamSynchronize(st), "amr transfer sync");
+    cudaFree(dmap);
+    if (s == PERRK_OK) hd->host_steps = hs->host_steps;
+    return s;
+}
+
 perrk_status perrk_test_stall_producer(perrk_ctx *h, int on) {
     if (!h) return PERRK_INVALID_ARG;
     h->c.ws_stall = on ? 1 : 0;

@@ -198,7 +198,20 @@ void df_tables(double gamma_gas, std::vector<float> &tab, std::vector<float> &co
 // in_u / in_uf into out_k / out_kf instead of the step buffers).
 perrk_status launch_stage(Ctx &c, int stage, bool rhs_only, const double *in_u, const float *in_uf, double *out_k,
                           float *out_kf, void *stream);
-perrk_status launch_mortars(Ctx &c, int stage, bool rhs_only, const double *in_u, const float *in_uf, void *stream);
+void mortar_operators(const std::vector<double> &x, double *P, double *R);
+
+// AMR (kernels_amr.cu): indicator constants, transfer operators
+struct AmrIndicatorConsts {
+    double Vinv[16];   // Vinv[a * 4 + i]: orthonormal Legendre coefficient a from nodal value i (one direction)
+    double T, s;       // threshold and sharpness of the indicator
+};
+struct AmrOps {
+    double P[32], R[32];   // the mortars' half-interval interpolation / projection, index (m 4 + j) 4 + i
+};
+void amr_indicator_consts(const std::vector<double> &x, AmrIndicatorConsts &K);
+perrk_status launch_amr_indicator(const Ctx &c, const AmrIndicatorConsts &K, double *alpha, void *stream);
+perrk_status launch_amr_transfer(const Ctx &src, Ctx &dst, const int32_t *map_dev, const AmrOps &O, void *stream);
+perrk_status launch_amr_history(const Ctx &src, Ctx &dst, void *stream);
 perrk_status launch_convert(const double *src_d, float *dst_f, const float *src_f, double *dst_d, size_t n,
                             void *stream);
 // float pair -> float64 (hi + lo); the split (hi = round(x), lo = round(x - hi))

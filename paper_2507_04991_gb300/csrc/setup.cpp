@@ -49,6 +49,39 @@ int min_E(int p) { return p == 2 ? 2 : (p == 3 ? 3 : 5); }
 int node_index(int dim, int i, int j, int k) { return i + 4 * j + (dim == 3 ? 16 * k : 0); }
 
 // Face node kk of face f: node index inside the element.
+int face_node(int dim, int f, int kk) {
+    int k = f / 2, s = f % 2, e = s ? 3 : 0;
+    if (dim == 1) return e;
+    if (dim == 2) return k == 0 ? e + 4 * kk : kk + 4 * e;
+    int a = kk % 4, b = kk / 4;
+    if (k == 0) return e + 4 * a + 16 * b;
+    if (k == 1) return a + 4 * e + 16 * b;
+    return a + 4 * b + 16 * e;
+}
+
+struct ElemGeo {
+    // derivative of coordinate comp along reference direction k at each node
+    double dx[3][3][64];
+};
+
+void elem_derivatives(int dim, const double *xe, const std::vector<double> &D, ElemGeo &g) {
+    const int NP = ipow4(dim);
+    for (int k = 0; k < dim; ++k)
+        for (int comp = 0; comp < dim; ++comp)
+            for (int q = 0; q < NP; ++q) {
+                int idx[3] = {q % 4, (q / 4) % 4, q / 16};
+                double acc = 0.0;
+                for (int m = 0; m < 4; ++m) {
+                    int id2[3] = {idx[0], idx[1], idx[2]};
+                    id2[k] = m;
+                    acc += D[idx[k] * 4 + m] * xe[node_index(dim, id2[0], id2[1], id2[2]) * dim + comp];
+                }
+                g.dx[k][comp][q] = acc;
+            }
+}
+
+}  // namespace
+
 // Lagrange basis of the LGL nodes x at the point s (extended precision).
 static void lagrange_at(const std::vector<double> &x, long double s, long double *l) {
     const int n = (int)x.size();
@@ -109,38 +142,6 @@ void mortar_operators(const std::vector<double> &x, double *P, double *R) {
     }
 }
 
-int face_node(int dim, int f, int kk) {
-    int k = f / 2, s = f % 2, e = s ? 3 : 0;
-    if (dim == 1) return e;
-    if (dim == 2) return k == 0 ? e + 4 * kk : kk + 4 * e;
-    int a = kk % 4, b = kk / 4;
-    if (k == 0) return e + 4 * a + 16 * b;
-    if (k == 1) return a + 4 * e + 16 * b;
-    return a + 4 * b + 16 * e;
-}
-
-struct ElemGeo {
-    // derivative of coordinate comp along reference direction k at each node
-    double dx[3][3][64];
-};
-
-void elem_derivatives(int dim, const double *xe, const std::vector<double> &D, ElemGeo &g) {
-    const int NP = ipow4(dim);
-    for (int k = 0; k < dim; ++k)
-        for (int comp = 0; comp < dim; ++comp)
-            for (int q = 0; q < NP; ++q) {
-                int idx[3] = {q % 4, (q / 4) % 4, q / 16};
-                double acc = 0.0;
-                for (int m = 0; m < 4; ++m) {
-                    int id2[3] = {idx[0], idx[1], idx[2]};
-                    id2[k] = m;
-                    acc += D[idx[k] * 4 + m] * xe[node_index(dim, id2[0], id2[1], id2[2]) * dim + comp];
-                }
-                g.dx[k][comp][q] = acc;
-            }
-}
-
-}  // namespace
 
 perrk_status build_ctx(Ctx &c, int n, const perrk_mesh_desc *mesh, const perrk_scheme_desc *scheme,
                        const perrk_options *opts, std::string &err) {
