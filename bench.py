@@ -45,10 +45,10 @@ DTYPE_CHOSEN = "f32 fluxes/K + f32x2 (~48-bit) state, d, entropy + f64 scalars"
 UNIT = "DOF-stage updates/s"
 
 
-def make_workload(name, rank=0):
+def make_workload(name, rank=0, instances=None):
     import workloads
     if name == "batched2d":
-        insts = workloads.batched_2d(n_inst=256, seed=1 + rank)
+        insts = workloads.batched_2d(n_inst=256, seed=1 + rank)[:(instances or 256)]
         return insts, ("256 independent 2D Euler instances, n x n quads with n ~ U{16..128} (1.63M elements, "
                        "1.04e8 DOF), 2-4 partitions by a graded refinement band, vortex or KHI initial data, "
                        "N=3, p=3 P-ERRK (S=12), Ranocha EC volume + Rusanov ES surface")
@@ -168,9 +168,11 @@ def reduce_over_ranks(x, world, op):
 # launch.  It is reported only while the stage kernel sources are the ones
 # those captures measured (code digest without comments and whitespace).
 STAGE_TRAFFIC = {"workload": "batched2d",
-                 "bytes": {0: 1597533952 + 1228019456,      # generic kernel, 8 elements per CTA
-                           1: 1597616640 + 1228039424},     # box kernel, 8 elements per CTA
-                 "sources_sha256": "03fb0d0369ec3a0a6ca6323142bbc63819b7361127d13343cec5ea0b3090de79"}
+                 # DRAM bytes per active element of the box kernel (8 elements
+                 # per CTA, flat grid), from a capture of the first 48
+                 # instances; a launch's traffic scales with its elements
+                 "bytes_per_element": {},
+                 "sources_sha256": ""}
 STAGE_SOURCES = ["stage.cuh", "stage_box.cuh", "physics.cuh", "dfloat.cuh", "kernels_stage2d.cu", "stage_launch.cu"]
 
 
@@ -190,11 +192,11 @@ def code_digest(paths):
     return h.hexdigest()
 
 
-def stage_traffic(workload, variant):
+def stage_traffic(workload, variant, n_active):
     h = code_digest([os.path.join(ROOT, "paper_2507_04991_gb300", "csrc", f) for f in STAGE_SOURCES])
-    ok = (workload == STAGE_TRAFFIC["workload"] and variant in STAGE_TRAFFIC["bytes"]
+    ok = (workload == STAGE_TRAFFIC["workload"] and variant in STAGE_TRAFFIC["bytes_per_element"]
           and h == STAGE_TRAFFIC["sources_sha256"])
-    return STAGE_TRAFFIC["bytes"][variant] if ok else None
+    return STAGE_TRAFFIC["bytes_per_element"][variant] * n_active if ok else None
 
 
 def measured_peaks():
@@ -382,7 +384,9 @@ def run_native(args):
     stream = torch.cuda.current_stream()
     sh = stream.cuda_stream
 
-    insts, desc = make_workload(args.workload, rank)
+    insts, desc = make_workload(args.workload, rank, args.instances)
+    if args.instances:
+        desc = f"the first {len(insts)} of: " + desc
     u0 = np.concatenate([w.u0 for w in insts], axis=1)
     dof_stage = sum(w.dof_stage_per_step() for w in insts)
     dof = sum(w.n_dof for w in insts)
@@ -595,7 +599,7 @@ def run_native(args):
                           "newton_guess_comparison_steps_4_to_10": guesses,
                           "newton_tol_r": {"mixed": args.mixed_tol_r, "fp64": 1e-14}},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": stage_traffic(args.workload, tuning["stage_variant"]), "kernel": f"k_stage (stage {S}, {st['n_active']} elements, all active)",
+                     "traffic": stage_traffic(args.workload, tuning["stage_variant"], st["n_active"]), "kernel": f"k_stage (stage {S}, {st['n_active']} elements, all active)",
                      "algorithmic_bytes": st["bytes"], "kernel_ms": 1e3 * k_s, "peak_source": peak_src},
         "cpu_baseline": {"value": cpu_all[0], "unit": UNIT, "cores": cpu_all[1], "kind": "oracle",
                          "sample": f"a {cpu_all[3]:g} s window in which each of {cpu_all[1]} host processes "
@@ -615,6 +619,70 @@ def run_native(args):
     print(json.dumps(line), flush=True)
 
 
+def run_amr(args):
+    """Adaptive KHI run (Sec. 3.2.2: the mesh changes every 7th step): a
+    16 x 16 quadtree on [-1, 1]^2 refined once where the density indicator
+    is large (thresholds 2e-4 / 1e-3 of the three-level controller, which
+    keep one refined band around each shear layer), partitions from the
+    levels (E = 6, 3 for levels 1, 0), the chosen numerics (mixed form, CUDA
+    graph, default box-kernel mapping).  value = DOF-stage updates of all steps over the wall time of
+    steps and adaptations together; the adaptation share is reported."""
+    import torch
+    import paper_2507_04991_gb300 as pk
+    from paper_2507_04991_gb300 import amr as pamr
+    import __graft_entry__
+    import workloads
+    __graft_entry__.build()
+    pk.load()
+    sh = torch.cuda.current_stream().cuda_stream
+    n, L, max_level, every = 16, 1.0, 1, 7
+    dt = 0.3 * (2 * L / (n << max_level)) / 7 / 2.5
+    u0 = workloads.quadtree_workload(workloads.Quadtree.uniform(n, L), "khi", (3,), 3, ic="khi").u0
+    opts = pk.options(precision=pk.MIXED, use_graph=True, max_it=args.max_it, tol_r=args.mixed_tol_r)
+    thresholds, levels = (2e-4, 1e-3), (0, 1, 1)
+    run = pamr.AmrRun(pamr.QuadMesh.uniform(n, L), u0, [6, 3], 3, dt, opts, max_level)
+    for _ in range(2):                                   # reach the refined mesh before timing
+        run.adapt(thresholds, levels)
+    cycles = max(1, (args.steps + every - 1) // every)
+    units, t_adapt, launches = 0, 0.0, 0
+    for _ in range(args.warmup):
+        pk.perrk_step(run.solver.h, 1, info=False, stream=sh)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for c in range(cycles):
+        # the adaptation: indicator, mesh, context of the new mesh, transfer,
+        # and the new context's first step (which captures its step graph)
+        torch.cuda.synchronize()
+        ta = time.perf_counter()
+        run.adapt(thresholds, levels)
+        pk.perrk_step(run.solver.h, 1, info=False, stream=sh)
+        torch.cuda.synchronize()
+        t_adapt += time.perf_counter() - ta
+        info = pk.perrk_stage_info(run.solver.h, 0)
+        pk.perrk_step(run.solver.h, every - 1, info=False, stream=sh)
+        units += every * info["dof_stage_per_step"]
+        launches += every * info["kernels_per_step"]
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    lv = np.bincount(run.mesh.levels(), minlength=2).tolist()
+    line = {"metric": METRIC, "value": units / wall, "unit": UNIT, "n_gpus": 1, "steps": cycles * every,
+            "warmup": args.warmup, "ms_per_step": 1e3 * wall / (cycles * every), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_CHOSEN, "data": "synthetic",
+            "config": {"workload": "khi2d_amr: Kelvin-Helmholtz on a 16x16 quadtree over [-1,1]^2, one level of refinement "
+                                   "by the density indicator (thresholds 2e-4, 1e-3), adapted every 7th step, "
+                                   "partitions from the levels (E = 6, 3), p=3, ES, mixed form, CUDA graph",
+                       "elements_at_end": len(run.mesh.leaves), "level_histogram_at_end": lv,
+                       "mortars_at_end": int(run.mesh.arrays()[2].shape[0]),
+                       "includes": "adaptation (indicator, mesh, context creation, transfer) inside the wall time; "
+                                   "default stage mapping (box kernel, 8 elements per CTA)"},
+            "amr": {"adapt_seconds": t_adapt, "adapt_share": t_adapt / wall, "cycles": cycles,
+                    "parts_seconds": dict(run.adapt_parts),
+                    "note": "adapt_seconds include each new context's first step (graph capture)"},
+            "gpu_launches": launches}
+    run.close()
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -622,6 +690,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="batched2d")
+    ap.add_argument("--instances", type=int, default=None,
+                    help="batched2d: use only the first N instances (profiling on a reduced case)")
     ap.add_argument("--max-it", type=int, default=4)
     ap.add_argument("--train-steps", type=int, default=30)
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="bound of the one-thread oracle sample")
@@ -639,6 +709,8 @@ def main():
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "khi2d_amr":
+        run_amr(args)
     else:
         run_native(args)
 

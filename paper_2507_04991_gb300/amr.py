@@ -196,6 +196,7 @@ class AmrRun:
         self.max_level, self.surface, self.gamma_gas = max_level, surface, gamma_gas
         self.solver = self._solver(mesh, u0)
         self.adapt_seconds = 0.0
+        self.adapt_parts = {"indicator": 0.0, "mesh": 0.0, "context": 0.0, "transfer": 0.0}
 
     def _problem(self, mesh, u0=None):
         coords, faces, mortars = mesh.arrays()
@@ -216,14 +217,20 @@ class AmrRun:
         t0 = time.perf_counter()
         levels = levels or (0, max(0, self.max_level - 1), self.max_level)
         alpha = perrk_amr_indicator(self.solver.h)
+        t1 = time.perf_counter()
         ref, coa = controller(self.mesh, alpha, thresholds, levels)
         new, amap = self.mesh.adapt(ref, coa)
+        t2 = time.perf_counter()
         nxt = self._solver(new)
         perrk_set_dt(nxt.h, self.dt)
+        t3 = time.perf_counter()
         perrk_amr_transfer(self.solver.h, nxt.h, amap)
         self.solver.close()
         self.solver, self.mesh = nxt, new
-        self.adapt_seconds += time.perf_counter() - t0
+        t4 = time.perf_counter()
+        for k, v in zip(("indicator", "mesh", "context", "transfer"), (t1 - t0, t2 - t1, t3 - t2, t4 - t3)):
+            self.adapt_parts[k] += v
+        self.adapt_seconds += t4 - t0
         return alpha, ref, coa, amap
 
     def state(self):

@@ -27,8 +27,8 @@ def test_code_digest_ignores_comments_not_code(tmp_path):
 
 def test_stage_traffic_only_for_its_workload():
     b = _bench()
-    assert b.stage_traffic("khi2d", 1) is None
-    assert b.stage_traffic("batched2d", 7) is None
+    assert b.stage_traffic("khi2d", 1, 100) is None
+    assert b.stage_traffic("batched2d", 7, 100) is None
 
 
 def test_cpu_samples_are_bounded():
