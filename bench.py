@@ -169,10 +169,11 @@ def reduce_over_ranks(x, world, op):
 # those captures measured (code digest without comments and whitespace).
 STAGE_TRAFFIC = {"workload": "batched2d",
                  # DRAM bytes per active element of the box kernel (8 elements
-                 # per CTA, flat grid), from a capture of the first 48
-                 # instances; a launch's traffic scales with its elements
-                 "bytes_per_element": {},
-                 "sources_sha256": ""}
+                 # per CTA, flat grid) at the all-active last stage, from a
+                 # capture of the first 128 instances (inputs well above L2);
+                 # a launch's traffic scales with its elements
+                 "bytes_per_element": {1: (748182528 + 559506944) / 763942},   # 128 instances, 0.977 of algorithmic
+                 "sources_sha256": "eaa884cd3b04dcc68510a913aca7d71d5710a6dccf9acca35fad2ae6f80f7e69"}
 STAGE_SOURCES = ["stage.cuh", "stage_box.cuh", "physics.cuh", "dfloat.cuh", "kernels_stage2d.cu", "stage_launch.cu"]
 
 
