@@ -335,6 +335,38 @@ perrk_status perrk_set_tuning(perrk_ctx *ctx, int elems_per_cta, int persistent_
 perrk_status perrk_amr_indicator(perrk_ctx *ctx, double *alpha, void *stream);
 perrk_status perrk_amr_transfer(const perrk_ctx *src, perrk_ctx *dst, const int32_t *map, void *stream);
 
+/* The adaptive runs' mesh (host only, no GPU): a 2:1-balanced periodic
+ * quadtree of square cells on [-L, L]^2 over an n x n base grid.  A leaf is
+ * (level, ix, iy), 0 <= ix, iy < n 2^level, with the cell
+ * [-L + ix h, -L + (ix+1) h] x [-L + iy h, -L + (iy+1) h], h = 2L / (n 2^level);
+ * leaves are kept in the canonical order of (level, ix, iy).
+ *
+ * perrk_quadtree_create: the uniform tree (n x n leaves at level 0).
+ * perrk_quadtree_leaves: out[n_leaves][3] = (level, ix, iy).
+ * perrk_quadtree_adapt: marks[n_leaves] (+1 refine, -1 coarsen, 0 keep).
+ * Families whose four leaves are all marked -1 (and none +1) merge, in
+ * descending (level, ix, iy) order of the parent, unless a face neighbour
+ * of the parent would then be two levels finer; leaves marked +1 split;
+ * then leaves are split until every face neighbour differs by at most one
+ * level.  The tree is replaced by the new one; map (caller-allocated,
+ * map_cap rows of 5; 4 x the old leaf count always suffices) receives the
+ * rows of perrk_amr_transfer for the new leaves, *n_new their count.
+ * perrk_quadtree_mesh: the mesh arrays of perrk_mesh_desc for the current
+ * leaves: coords [n_leaves][16][2] (LGL nodes), faces [n_faces][4]
+ * (conforming pairs), mortars [n_mortars][4] (2:1 rows), levels [n_leaves];
+ * any output may be NULL (call once with NULLs to get n_faces, n_mortars:
+ * at most 2 and 4 per leaf).  INVALID_ARG for null arguments, a map
+ * capacity below the new count, or a refinement beyond n 2^level = 2^29
+ * cells per direction. */
+typedef struct perrk_quadtree perrk_quadtree;
+perrk_status perrk_quadtree_create(int n, double L, perrk_quadtree **out);
+void perrk_quadtree_destroy(perrk_quadtree *tree);
+int perrk_quadtree_size(const perrk_quadtree *tree);
+perrk_status perrk_quadtree_leaves(const perrk_quadtree *tree, int32_t *out);
+perrk_status perrk_quadtree_adapt(perrk_quadtree *tree, const int8_t *marks, int32_t *map, int map_cap, int *n_new);
+perrk_status perrk_quadtree_mesh(const perrk_quadtree *tree, double *coords, int32_t *faces, int *n_faces,
+                                 int32_t *mortars, int *n_mortars, int32_t *levels);
+
 /* Test hook (the paper has no counterpart): with on != 0, the producer warp
  * of stage kernel variants 3 and 4 fills no staging buffer, so that its consumer
  * warps' bounded waits run out after about one second each; the next

@@ -35,7 +35,9 @@ EXPORTED = [
     "perrk_rhs", "perrk_mlp_size", "perrk_mlp_features", "perrk_set_mlp", "perrk_mlp_train", "perrk_mlp_grad",
     "perrk_last_error", "perrk_status_string", "perrk_launch_stage", "perrk_stage_info", "perrk_df_log", "perrk_autotune", "perrk_tuning", "perrk_set_tuning", "perrk_entropy_static", "perrk_checkpoint_size",
     "perrk_checkpoint_save", "perrk_checkpoint_load", "perrk_fma_peak",
-    "perrk_test_stall_producer", "perrk_amr_indicator", "perrk_amr_transfer",
+    "perrk_test_stall_producer", "perrk_amr_indicator", "perrk_amr_transfer", "perrk_quadtree_create",
+    "perrk_quadtree_destroy", "perrk_quadtree_size", "perrk_quadtree_leaves", "perrk_quadtree_adapt",
+    "perrk_quadtree_mesh",
 ]
 
 
@@ -117,6 +119,12 @@ def load(path=LIB_PATH):
         "perrk_test_stall_producer": (I, [P, I]),
         "perrk_amr_indicator": (I, [P, P, P]),
         "perrk_amr_transfer": (I, [P, P, P, P]),
+        "perrk_quadtree_create": (I, [I, D, P]),
+        "perrk_quadtree_destroy": (V, [P]),
+        "perrk_quadtree_size": (I, [P]),
+        "perrk_quadtree_leaves": (I, [P, P]),
+        "perrk_quadtree_adapt": (I, [P, P, P, I, P]),
+        "perrk_quadtree_mesh": (I, [P, P, P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

@@ -12,7 +12,7 @@ BUILD = os.path.join(os.path.dirname(HERE), "_build")
 LIB = os.path.join(HERE, "libperrk.so")
 SOURCES = ["setup.cpp", "api.cu", "stage_launch.cu", "kernels_stage1d.cu", "kernels_stage2d.cu",
            "kernels_stage3d.cu", "kernels_relax.cu", "mlp.cu", "entropy_static.cu",
-           "kernels_visc.cu", "peaks.cu", "kernels_mortar.cu", "kernels_amr.cu"]
+           "kernels_visc.cu", "peaks.cu", "kernels_mortar.cu", "kernels_amr.cu", "quadtree.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

@@ -8,11 +8,11 @@ partitions are re-derived from the new element sizes (Sec. 2.2: a cell of
 half the size gets the member with twice the stage evaluations).  Interfaces
 between cells of different levels are 2:1 mortars.
 
-Host logic only (argument preparation for the library): the quadtree with
-its 2:1 balance, the three-level controller, the mesh arrays of the C ABI and
-the partition ids.  The two computations on the state run in the library's
-kernels: the indicator (perrk_amr_indicator) and the transfer
-(perrk_amr_transfer).
+The quadtree with its 2:1 balance, its adaptation and the mesh arrays of the
+C ABI are the library's native host code (perrk_quadtree_*); this module adds
+the three-level controller, the partition ids and the driver.  The two
+computations on the state run in the library's kernels: the indicator
+(perrk_amr_indicator) and the transfer (perrk_amr_transfer).
 
 Canonical orders: leaves sorted by (level, ix, iy); a leaf's cell is
 [-L + ix h, -L + (ix + 1) h] x [-L + iy h, ...], h = 2L / (n 2^level), on the
@@ -20,139 +20,115 @@ periodic square [-L, L]^2 over an n x n base grid.
 """
 from __future__ import annotations
 
-import math
+import ctypes as C
 
 import numpy as np
 
-from . import Solver, perrk_amr_indicator, perrk_amr_transfer, perrk_set_dt
-
-_LGL = np.array([-1.0, -1.0 / math.sqrt(5.0), 1.0 / math.sqrt(5.0), 1.0])
+from . import Solver, _check, _ptr, load as _lib, perrk_amr_indicator, perrk_amr_transfer, perrk_set_dt
 
 
 class QuadMesh:
-    """A 2:1-balanced periodic quadtree (see the module docstring)."""
+    """A 2:1-balanced periodic quadtree (see the module docstring), held by
+    the library's native quadtree (perrk_quadtree_*).  `leaves` lists
+    (level, ix, iy) in the canonical order; adapt() hands the native tree on
+    to the mesh it returns."""
 
-    def __init__(self, n, L, leaves):
+    def __init__(self, n, L, handle):
         self.n, self.L = int(n), float(L)
-        self.leaves = sorted(set(leaves))
-        self.pos = {c: k for k, c in enumerate(self.leaves)}
+        self._h = handle
+        cnt = _lib().perrk_quadtree_size(handle)
+        buf = np.empty((cnt, 3), dtype=np.int32)
+        _check(_lib().perrk_quadtree_leaves(handle, _ptr(buf)), "perrk_quadtree_leaves")
+        self.leaf_array = buf                      # [n_leaves][3] = (level, ix, iy)
+        self._leaves = None
+        self._pos = None
+
+    def __len__(self):
+        return len(self.leaf_array)
+
+    @property
+    def leaves(self):
+        """(level, ix, iy) tuples in the canonical order (built on first use)."""
+        if self._leaves is None:
+            self._leaves = [tuple(r) for r in self.leaf_array.tolist()]
+        return self._leaves
+
+    @property
+    def pos(self):
+        if self._pos is None:
+            self._pos = {c: k for k, c in enumerate(self.leaves)}
+        return self._pos
 
     @classmethod
     def uniform(cls, n, L):
-        return cls(n, L, [(0, i, j) for i in range(n) for j in range(n)])
+        h = C.c_void_p()
+        _check(_lib().perrk_quadtree_create(int(n), float(L), C.byref(h)), "perrk_quadtree_create")
+        return cls(n, L, h)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            try:
+                _lib().perrk_quadtree_destroy(h)
+            except Exception:
+                pass
+            self._h = None
 
     def size(self, lev):
         return 2.0 * self.L / (self.n << lev)
 
-    def _wrap(self, lev, i, j):
+    def owner(self, lev, i, j):
+        """Leaf containing cell (lev, i, j) (periodic), or None where that cell is split."""
         m = self.n << lev
-        return lev, i % m, j % m
-
-    def owner(self, lev, i, j, leaves=None):
-        """Leaf containing cell (lev, i, j), or None where that cell is split."""
-        leaves = self.pos if leaves is None else leaves
-        lev, i, j = self._wrap(lev, i, j)
+        i, j = i % m, j % m
         while lev >= 0:
-            if (lev, i, j) in leaves:
+            if (lev, i, j) in self.pos:
                 return (lev, i, j)
             lev, i, j = lev - 1, i // 2, j // 2
         return None
-
-    @staticmethod
-    def _children(c):
-        lev, i, j = c
-        return [(lev + 1, 2 * i + (k & 1), 2 * j + (k >> 1)) for k in range(4)]   # child index a + 2 b
-
-    def _balance(self, leaves):
-        """Split leaves until no face neighbour is two levels finer."""
-        leaves = set(leaves)
-        queue = sorted(leaves, reverse=True)
-        while queue:
-            c = queue.pop()
-            if c not in leaves:
-                continue
-            lev, i, j = c
-            for di, dj in ((1, 0), (-1, 0), (0, 1), (0, -1)):
-                o = self.owner(lev, i + di, j + dj, leaves)
-                if o is not None and o[0] < lev - 1:
-                    leaves.discard(o)
-                    kids = self._children(o)
-                    leaves.update(kids)
-                    queue.extend(kids)
-                    queue.append(c)
-        return leaves
 
     def adapt(self, refine, coarsen):
         """New mesh and the map of its leaves (rows kind, a0..a3 as in
         perrk_amr_transfer): families all marked for coarsening (and none of
         whose members is marked for refinement) merge unless that breaks the
-        balance, marked leaves split, and the balance is restored."""
-        refine = set(refine)
-        coarsen = set(coarsen) - refine
-        leaves = set(self.leaves)
-        parents = sorted({(l - 1, i // 2, j // 2) for (l, i, j) in coarsen if l > 0}, reverse=True)
-        for p in parents:
-            kids = self._children(p)
-            if not all(k in leaves and k in coarsen for k in kids):
-                continue
-            trial = (leaves - set(kids)) | {p}
-            if self._balance(trial) == trial:
-                leaves = trial
+        balance, marked leaves split, and the balance is restored.  This
+        mesh object is spent (the native tree moves to the new one)."""
+        marks = np.zeros(len(self), dtype=np.int8)
+        for c in coarsen:
+            marks[self.pos[c]] = -1
         for c in refine:
-            if c in leaves:
-                leaves.discard(c)
-                leaves.update(self._children(c))
-        new = QuadMesh(self.n, self.L, self._balance(leaves))
-        rows = []
-        for c in new.leaves:
-            if c in self.pos:
-                rows.append((0, self.pos[c], 0, 0, 0))
-                continue
-            lev, i, j = c
-            par = (lev - 1, i // 2, j // 2)
-            if lev > 0 and par in self.pos:
-                rows.append((1, self.pos[par], (i & 1) + 2 * (j & 1), 0, 0))
-                continue
-            kids = self._children(c)
-            if not all(k in self.pos for k in kids):
-                raise ValueError("a leaf changed by more than one level in one adaptation")
-            rows.append((2,) + tuple(self.pos[k] for k in kids))
-        return new, np.asarray(rows, dtype=np.int32).reshape(-1, 5)
+            marks[self.pos[c]] = 1
+        return self.adapt_marks(marks)
+
+    def adapt_marks(self, marks):
+        """adapt() with the marks as an array over the leaves (+1 refine,
+        -1 coarsen, 0 keep)."""
+        if not self._h:
+            raise RuntimeError("this quadtree mesh was already adapted")
+        marks = np.ascontiguousarray(marks, dtype=np.int8)
+        cap = 4 * len(self)
+        amap = np.empty((cap, 5), dtype=np.int32)
+        n_new = C.c_int(0)
+        _check(_lib().perrk_quadtree_adapt(self._h, _ptr(marks), _ptr(amap), cap, C.byref(n_new)),
+               "perrk_quadtree_adapt")
+        h, self._h = self._h, None
+        return QuadMesh(self.n, self.L, h), amap[:n_new.value].copy()
 
     def levels(self):
-        return np.array([c[0] for c in self.leaves], dtype=np.int32)
+        return self.leaf_array[:, 0].copy()
 
     def arrays(self):
         """(node coordinates [n_elem, 16, 2], conforming faces [n, 4],
         mortars [n, 4]) in the conventions of perrk_mesh_desc."""
-        t = 0.5 * (_LGL + 1.0)
-        q = np.arange(16)
-        coords = np.empty((len(self.leaves), 16, 2))
-        faces, mortars = [], []
-        for e, (lev, i, j) in enumerate(self.leaves):
-            h = self.size(lev)
-            coords[e, :, 0] = -self.L + (i + t[q & 3]) * h
-            coords[e, :, 1] = -self.L + (j + t[q >> 2]) * h
-            # face 0: -x, 1: +x, 2: -y, 3: +y
-            for f, (di, dj) in enumerate(((-1, 0), (1, 0), (0, -1), (0, 1))):
-                nb = self._wrap(lev, i + di, j + dj)
-                if nb in self.pos:
-                    if f % 2 == 1:
-                        faces.append((e, f, self.pos[nb], f - 1))
-                    continue
-                o = self.owner(*nb)
-                if o is not None:
-                    continue                          # a coarser neighbour lists this face in its mortar row
-                ni, nj = nb[1], nb[2]
-                if f in (0, 1):                       # the finer column touching this face, lower y first
-                    ci = 2 * ni + (1 if f == 0 else 0)
-                    pair = ((lev + 1, ci, 2 * nj), (lev + 1, ci, 2 * nj + 1))
-                else:                                 # the finer row touching this face, lower x first
-                    cj = 2 * nj + (1 if f == 2 else 0)
-                    pair = ((lev + 1, 2 * ni, cj), (lev + 1, 2 * ni + 1, cj))
-                mortars.append((e, f, self.pos[pair[0]], self.pos[pair[1]]))
-        return (coords, np.asarray(faces, dtype=np.int32).reshape(-1, 4),
-                np.asarray(mortars, dtype=np.int32).reshape(-1, 4))
+        lib = _lib()
+        nf, nm = C.c_int(0), C.c_int(0)
+        _check(lib.perrk_quadtree_mesh(self._h, None, None, C.byref(nf), None, C.byref(nm), None), "perrk_quadtree_mesh")
+        coords = np.empty((len(self), 16, 2))
+        faces = np.empty((nf.value, 4), dtype=np.int32)
+        mortars = np.empty((nm.value, 4), dtype=np.int32)
+        _check(lib.perrk_quadtree_mesh(self._h, _ptr(coords), _ptr(faces) if nf.value else None, C.byref(nf),
+                                       _ptr(mortars) if nm.value else None, C.byref(nm), None), "perrk_quadtree_mesh")
+        return coords, faces, mortars
 
 
 def controller(mesh, alpha, thresholds=(0.01, 0.5), levels=(0, 1, 2)):
@@ -167,6 +143,15 @@ def controller(mesh, alpha, thresholds=(0.01, 0.5), levels=(0, 1, 2)):
         elif c[0] > target:
             coa.append(c)
     return ref, coa
+
+
+def controller_marks(mesh, alpha, thresholds=(0.01, 0.5), levels=(0, 1, 2)):
+    """The controller's decisions as marks over the leaves (+1 refine,
+    -1 coarsen, 0 keep), vectorised."""
+    a = np.asarray(alpha)
+    target = np.where(a >= thresholds[1], levels[2], np.where(a >= thresholds[0], levels[1], levels[0]))
+    lev = mesh.leaf_array[:, 0]
+    return np.where(lev < target, 1, np.where(lev > target, -1, 0)).astype(np.int8)
 
 
 class _Problem:
@@ -218,8 +203,9 @@ class AmrRun:
         levels = levels or (0, max(0, self.max_level - 1), self.max_level)
         alpha = perrk_amr_indicator(self.solver.h)
         t1 = time.perf_counter()
-        ref, coa = controller(self.mesh, alpha, thresholds, levels)
-        new, amap = self.mesh.adapt(ref, coa)
+        marks = controller_marks(self.mesh, alpha, thresholds, levels)
+        leaves = self.mesh.leaf_array
+        new, amap = self.mesh.adapt_marks(marks)
         t2 = time.perf_counter()
         nxt = self._solver(new)
         perrk_set_dt(nxt.h, self.dt)
@@ -231,6 +217,8 @@ class AmrRun:
         for k, v in zip(("indicator", "mesh", "context", "transfer"), (t1 - t0, t2 - t1, t3 - t2, t4 - t3)):
             self.adapt_parts[k] += v
         self.adapt_seconds += t4 - t0
+        ref = [tuple(c) for c in leaves[marks > 0].tolist()]
+        coa = [tuple(c) for c in leaves[marks < 0].tolist()]
         return alpha, ref, coa, amap
 
     def state(self):
