@@ -74,7 +74,7 @@ def make_workload(name, rank=0, instances=None):
 
 
 class ClockSampler:
-    """nvidia-smi SM clocks and throttle reasons sampled every 200 ms."""
+    """nvidia-smi SM clocks and throttle reasons sampled every 50 ms."""
 
     def __init__(self, gpu_index):
         self.samples = []
@@ -87,7 +87,7 @@ class ClockSampler:
              "clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
