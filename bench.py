@@ -8,7 +8,8 @@ partition r, summed over instances.
 
 Chosen form: all instances in one batched context (one launch per stage over
 every instance's active elements, per-instance Newton solves), FP32 fluxes
-with float64 state, direction, entropy reductions, Newton and update, the
+and stage registers, the state, direction, entropy passes and update as
+float pairs (~48-bit significand), float64 Newton scalars and Delta H, the
 learned Newton guess (trained during set-up on gamma traces of the plain
 method), autotuned CTA mapping, one CUDA graph per step.  It is compared with
 the plain float64 form looped per instance and with the plain float64 form
@@ -169,11 +170,12 @@ def reduce_over_ranks(x, world, op):
 # those captures measured (code digest without comments and whitespace).
 STAGE_TRAFFIC = {"workload": "batched2d",
                  # DRAM bytes per active element of the box kernel (8 elements
-                 # per CTA, flat grid) at the all-active last stage, from a
-                 # capture of the first 128 instances (inputs well above L2);
-                 # a launch's traffic scales with its elements
-                 "bytes_per_element": {1: (748182528 + 559506944) / 763942},   # 128 instances, 0.977 of algorithmic
-                 "sources_sha256": "eaa884cd3b04dcc68510a913aca7d71d5710a6dccf9acca35fad2ae6f80f7e69"}
+                 # per CTA, persistent grid of 3,040 CTAs) at the all-active
+                 # last stage, from a capture of the first 128 instances
+                 # (inputs well above L2); a launch's traffic scales with its
+                 # elements
+                 "bytes_per_element": {1: (771602176 + 558539008) / 763942},   # 128 instances, 0.994 of algorithmic
+                 "sources_sha256": "124f7330f1e9bb46e83981887e1bb1d52384cb52446a78fe70b59426fdd57983"}
 STAGE_SOURCES = ["stage.cuh", "stage_box.cuh", "physics.cuh", "dfloat.cuh", "kernels_stage2d.cu", "stage_launch.cu"]
 
 
@@ -582,9 +584,10 @@ def run_native(args):
         "vs_baseline": None, "dtype": DTYPE_CHOSEN, "data": "synthetic",
         "config": {"workload": f"{args.workload}: {desc}", "instances": len(insts), "dof": dof,
                    "dof_stage_per_step": dof_stage,
-                   "form": "chosen: batched instances, FP32 flux differencing and surface fluxes, float64 state, "
-                           "direction, entropy reductions (double-float entropy evaluation), Newton and update, "
-                           "learned Newton guess, autotuned mapping, one CUDA graph per step",
+                   "form": "chosen: batched instances, FP32 flux differencing, surface fluxes and stage registers "
+                           "K_i; state, direction, entropy passes and update as float pairs (~48-bit); float64 "
+                           "Newton scalars and Delta H; learned Newton guess, autotuned mapping, one CUDA graph "
+                           "per step",
                    "autotuned_mapping": tuning, "newton_max_it": args.max_it,
                    "l2": ("inputs larger than L2; " if big_l2 else "") + "L2 flushed (256 MiB write) before every timed step",
                    "parallelism": f"replicas x{world}"},

@@ -271,17 +271,19 @@ perrk_status perrk_checkpoint_save(perrk_ctx *ctx, void *buf, size_t size, void 
  * short; the context is unchanged then. */
 perrk_status perrk_checkpoint_load(perrk_ctx *ctx, const void *buf, size_t size, void *stream);
 
-/* Autotune the launch mapping of ctx on the current device: times the first
- * and the last stage kernel for every valid elements-per-CTA choice, grid
- * mapping (one CTA per element group, or a persistent grid of k CTAs per SM)
+/* Autotune the launch mapping of ctx on the current device: times the stage
+ * kernels of a whole step (every stage in order, as the step runs them) for
+ * every valid elements-per-CTA choice, grid mapping (one CTA per element
+ * group, or a persistent grid of k CTAs per SM, k = 2, 4, 8 and, for the box
+ * kernels, the k of exactly one resident wave)
  * and, for the mixed form on box elements, stage kernel variant (generic;
  * float4 box kernel; box kernel staging the next element group with
  * cp.async; in 2D the box kernel fed by a producer warp, two ways), then the
  * relaxation block size; keeps the fastest and
  * re-captures the step graph.  Results do not depend on the choice (same
  * per-element arithmetic in the same order).  Overwrites the stage registers
- * and d (call between steps).  best_ms_out (nullable): mean time of the chosen
- * stage launches.  Synchronises the stream. */
+ * and d (call between steps).  best_ms_out (nullable): mean time per stage
+ * launch of the chosen mapping.  Synchronises the stream. */
 perrk_status perrk_autotune(perrk_ctx *ctx, void *stream, float *best_ms_out);
 
 /* Current launch mapping (elements per CTA, persistent grid size or 0,

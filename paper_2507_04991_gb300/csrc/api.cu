@@ -527,8 +527,20 @@ perrk_status perrk_autotune(perrk_ctx *h, void *stream, float *best_ms_out) {
     const bool box = c.opt.precision == PERRK_MIXED && c.equation != PERRK_BURGERS_1D && !c.curved && c.dim >= 2;
     const std::vector<int> variants = box ? (c.dim == 2 ? std::vector<int>{0, 1, 2, 3, 4} : std::vector<int>{0, 1, 2})
                                           : std::vector<int>{c.stage_variant};
-    // timed launches: the first stage and the last (usually all elements active)
-    const int stages[2] = {0, c.S - 1};
+    // box kernels: also the persistent grids of exactly one wave (2D: 1280 /
+    // (16 EPB) resident CTAs per SM at 48 registers, i.e. 20, 10, 5 for
+    // EPB = 4, 8, 16; 3D: 768 / (64 EPB), i.e. 12, 6, 3 for EPB = 1, 2, 4)
+    if (box)
+        for (int k : c.dim == 2 ? std::vector<int>{5, 10, 20} : std::vector<int>{3, 6, 12}) grids.push_back(k * sms);
+    // timed: every stage of a step in order, as the step graph runs them
+    // (the stages with partial active prefixes weigh in), after a warm-up of
+    // the first and the last stage
+    auto sweep = [&]() {
+        bool ok = true;
+        for (int si = 0; si < c.S && ok; ++si)
+            ok = launch_stage(c, si, false, nullptr, nullptr, nullptr, nullptr, st) == PERRK_OK;
+        return ok;
+    };
     float best = 1e30f;
     int best_epb = c.stage_epb, best_grid = c.stage_persistent, best_var = c.stage_variant;
     const int save_epb = c.stage_epb, save_grid = c.stage_persistent, save_var = c.stage_variant;
@@ -538,24 +550,19 @@ perrk_status perrk_autotune(perrk_ctx *h, void *stream, float *best_ms_out) {
                 c.stage_variant = var;
                 c.stage_epb = epb;
                 c.stage_persistent = g;
-                // warm-up launches; an unsupported configuration reports an error and is skipped
-                bool ok = true;
-                for (int si : stages) ok = ok && launch_stage(c, si, false, nullptr, nullptr, nullptr, nullptr, st) == PERRK_OK;
+                // warm-up; an unsupported configuration reports an error and is skipped
+                bool ok = launch_stage(c, 0, false, nullptr, nullptr, nullptr, nullptr, st) == PERRK_OK &&
+                          launch_stage(c, c.S - 1, false, nullptr, nullptr, nullptr, nullptr, st) == PERRK_OK;
                 if (!ok) {
                     cudaGetLastError();
                     continue;
                 }
+                cudaEventRecord(e0, st);
+                ok = sweep();
+                cudaEventRecord(e1, st);
+                cudaEventSynchronize(e1);
                 float tot = 0.0f;
-                for (int rep = 0; rep < 3 && ok; ++rep)
-                    for (int si : stages) {
-                        cudaEventRecord(e0, st);
-                        ok = ok && launch_stage(c, si, false, nullptr, nullptr, nullptr, nullptr, st) == PERRK_OK;
-                        cudaEventRecord(e1, st);
-                        cudaEventSynchronize(e1);
-                        float ms = 0.0f;
-                        cudaEventElapsedTime(&ms, e0, e1);
-                        tot += ms;
-                    }
+                cudaEventElapsedTime(&tot, e0, e1);
                 if (ok && tot < best) {
                     best = tot;
                     best_epb = epb;
@@ -588,7 +595,7 @@ perrk_status perrk_autotune(perrk_ctx *h, void *stream, float *best_ms_out) {
     cudaEventDestroy(e1);
     c.tuned = true;
     c.graph_dirty = true;
-    if (best_ms_out) *best_ms_out = best / 6.0f;
+    if (best_ms_out) *best_ms_out = best / (float)c.S;
     return cuda_check((int)cudaStreamSynchronize(st), "autotune sync");
 }
 

@@ -44,6 +44,17 @@ cudaError_t stage_launch_2d(const StageParams &P, bool burgers, bool mixed, bool
 template <int EPB, bool PIPE>
 static cudaError_t box_go(const StageParams &P, int grid, cudaStream_t st) {
     if constexpr (stage_box_smem_bytes<2, EPB, PIPE>() <= 48 * 1024) {
+        if (P.face_mortar) {
+            // meshes with mortars (inviscid, no staging: the only combination
+            // the context accepts with mortars)
+            if constexpr (!PIPE) {
+                if (!P.visc_kv) {
+                    k_stage_box<2, EPB, false, false, true><<<grid, EPB * ipow4(2), 0, st>>>(P);
+                    return cudaGetLastError();
+                }
+            }
+            return cudaErrorNotSupported;
+        }
         if (P.visc_kv) k_stage_box<2, EPB, PIPE, true><<<grid, EPB * ipow4(2), 0, st>>>(P);
         else k_stage_box<2, EPB, PIPE, false><<<grid, EPB * ipow4(2), 0, st>>>(P);
         return cudaGetLastError();

@@ -292,8 +292,11 @@ constexpr int box_min_blocks() {
 }
 
 // VISC: add the viscous divergence visc_kv (Navier-Stokes-Fourier runs); the
-// inviscid instantiation carries no trace of it.
-template <int DIM, int EPB, bool PIPE, bool VISC>
+// inviscid instantiation carries no trace of it.  MORT: meshes with 2:1
+// mortars, whose element faces on a mortar take the mortar kernel's flux (a
+// separate instantiation, so that conforming meshes run without the extra
+// registers it needs).
+template <int DIM, int EPB, bool PIPE, bool VISC, bool MORT = false>
 __global__ void __launch_bounds__(EPB * ipow4(DIM), box_min_blocks<DIM, EPB, PIPE>()) k_stage_box(const StageParams P) {
     using B = BoxShape<DIM>;
     constexpr int NP = B::NP, NF = B::NF, V = B::V, NPAIR = B::NPAIR, PPT = B::PPT;
@@ -458,7 +461,7 @@ __global__ void __launch_bounds__(EPB * ipow4(DIM), box_min_blocks<DIM, EPB, PIP
                         fs[v] -= 0.5f * lam * (uR - uL);
                     }
                 }
-                if (P.face_mortar) {
+                if constexpr (MORT) {
                     // a 2:1 mortar face: the mortar kernel's flux for this element face
                     const int ms = __ldg(P.face_mortar + (size_t)e * NF + f);
                     if (ms >= 0) {
