@@ -175,7 +175,7 @@ STAGE_TRAFFIC = {"workload": "batched2d",
                  # (inputs well above L2); a launch's traffic scales with its
                  # elements
                  "bytes_per_element": {1: (771602176 + 558539008) / 763942},   # 128 instances, 0.994 of algorithmic
-                 "sources_sha256": "124f7330f1e9bb46e83981887e1bb1d52384cb52446a78fe70b59426fdd57983"}
+                 "sources_sha256": "717167492a36e766833b3ab225069deec51eb76f50b0a9fa1af51fd4c26d2dc4"}
 STAGE_SOURCES = ["stage.cuh", "stage_box.cuh", "physics.cuh", "dfloat.cuh", "kernels_stage2d.cu", "stage_launch.cu"]
 
 

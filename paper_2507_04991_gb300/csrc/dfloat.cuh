@@ -9,9 +9,11 @@
 // "Table-driven implementation of the logarithm function in IEEE
 // floating-point arithmetic"): x = 2^k m, m in [1,2), F = 1 + j/128 nearest
 // to m, r = (m - F)/F with |r| <= 2^-8, log x = k log 2 + log F + log1p(r),
-// log1p(r) = r - r^2/2 + r^3/3 - ... with the first three terms in df and the
-// tail from r^4 on in float.  log F and 1/F come from a host-built table
-// (long double, split into float pairs).
+// log1p(r) = r - r^2/2 + r^2 c with c = r/3 - r^2/4 + r^3/5 - r^4/6: r and
+// r^2/2 in df, the term r^2 c (below 2^-25) in float, whose rounding (about
+// 2^-49) and the series' truncation (r^7/7, below 2^-58) stay under the df
+// rounding of the sum.  log F and 1/F come from a host-built table (long
+// double, split into float pairs).
 #pragma once
 
 #include <cstdint>
@@ -23,7 +25,7 @@ struct df {
 };
 
 struct DfConst {
-    df ln2, third, gm1, gam;   // log 2, 1/3, gamma - 1, gamma as float pairs
+    df ln2, gm1, gam;   // log 2, gamma - 1, gamma as float pairs
 };
 
 __device__ __forceinline__ df df_two_sum(float a, float b) {
@@ -80,6 +82,12 @@ __device__ __forceinline__ df df_rcp(df x) {
 // x + y f (df plus df times float)
 __device__ __forceinline__ df df_fma_f(df x, df y, float f) { return df_add(x, df_mul_f(y, f)); }
 
+// x + f (df plus float)
+__device__ __forceinline__ df df_add_f(df x, float f) {
+    const df s = df_two_sum(x.hi, f);
+    return df_fast(s.hi, s.lo + x.lo);
+}
+
 // float64 -> df (one FP64 subtraction) and back (one FP64 addition).
 __device__ __forceinline__ df df_from(double d) {
     const float hi = __double2float_rn(d);
@@ -101,10 +109,9 @@ __device__ __forceinline__ df df_log(df x, const float4 *__restrict__ tab, const
     const df d = df_two_sum(mh - F, ml);
     const df r = df_mul(d, df{t.z, t.w});
     const float rh = r.hi;
-    const float tail = fmaf(rh, fmaf(rh, fmaf(rh, 1.0f / 7.0f, -1.0f / 6.0f), 1.0f / 5.0f), -0.25f);
-    const df inner = df_add(K.third, df_mul_f(r, tail));             // 1/3 + r t
-    const df inner2 = df_add(df{-0.5f, 0.0f}, df_mul(r, inner));      // -1/2 + r (...)
-    const df l1p = df_add(r, df_mul(r, df_mul(r, inner2)));           // r + r^2 (...)
+    const float c = rh * fmaf(rh, fmaf(rh, fmaf(rh, -1.0f / 6.0f, 0.2f), -0.25f), 1.0f / 3.0f);
+    const df r2 = df_mul(r, r);
+    const df l1p = df_add_f(df_add(r, df{-0.5f * r2.hi, -0.5f * r2.lo}), r2.hi * c);   // r - r^2/2 + r^2 c
     const df kl = df_mul_f(K.ln2, (float)k);
     return df_add(df_add(kl, df{t.x, t.y}), l1p);
 }

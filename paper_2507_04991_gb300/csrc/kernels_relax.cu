@@ -667,7 +667,6 @@ static RelaxParams relax_params(Ctx &c) {
     P.br_hi = c.opt.bracket_hi;
     P.dftab = (const float4 *)c.g_dftab;
     P.K.ln2 = df{c.df_consts[0], c.df_consts[1]};
-    P.K.third = df{c.df_consts[2], c.df_consts[3]};
     P.K.gm1 = df{c.df_consts[4], c.df_consts[5]};
     P.K.gam = df{c.df_consts[6], c.df_consts[7]};
     return P;
@@ -704,7 +703,6 @@ __global__ void k_df_log(const float4 *tab, const float *kc, const double *x, do
     if (i >= n) return;
     DfConst K;
     K.ln2 = df{kc[0], kc[1]};
-    K.third = df{kc[2], kc[3]};
     y[i] = df_to(df_log(df_from(x[i]), tab, K));
 }
 

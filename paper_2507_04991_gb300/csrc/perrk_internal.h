@@ -167,7 +167,7 @@ struct Ctx {
     float *g_mlp = nullptr;                   // weights (nullptr: no MLP)
     float *g_dftab = nullptr;                 // double-float log table [129][4]
     void *g_box_tab = nullptr;                // box stage kernels: per-node work table
-    float df_consts[8] = {0};                 // log 2, 1/3, gamma-1, gamma (float pairs)
+    float df_consts[8] = {0};                 // log 2, (unused), gamma-1, gamma (float pairs)
     int mlp_on = 0;
 
     // launch configuration (autotuned)

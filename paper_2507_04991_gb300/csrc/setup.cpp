@@ -667,7 +667,7 @@ void stage_coefficients(const Ctx &c, std::vector<StageCoef> &coef, std::vector<
 
 // Tables of the double-float logarithm: for F_j = 1 + j/128 (j = 0..128)
 // log F_j and 1/F_j in long double, each split into a float pair; constants
-// log 2, 1/3, gamma - 1 and gamma as float pairs.
+// log 2, (slots 2-3 unused), gamma - 1 and gamma as float pairs.
 static void split2(long double v, float &hi, float &lo) {
     hi = (float)v;
     lo = (float)(v - (long double)hi);
@@ -682,7 +682,6 @@ void df_tables(double gamma_gas, std::vector<float> &tab, std::vector<float> &co
     }
     consts.assign(8, 0.0f);
     split2(std::log(2.0L), consts[0], consts[1]);
-    split2(1.0L / 3.0L, consts[2], consts[3]);
     split2((long double)gamma_gas - 1.0L, consts[4], consts[5]);
     split2((long double)gamma_gas, consts[6], consts[7]);
 }
