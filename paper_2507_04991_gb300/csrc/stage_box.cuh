@@ -40,6 +40,18 @@ struct BoxShape {
     static constexpr int X = DIM == 3 ? 1 : 0;                // 3D: fifth component beside a float4
 };
 
+// Face slot that thread q takes in face round t (or -1): rounds 0 .. FPT - 2
+// take slot q + NP t; a partial last round (3D: 96 face slots over 64
+// threads) goes to the upper threads, so that it does not fall on the same
+// warps as the partial last round of node pairs (pairs q + NP t go to the
+// lower threads).
+template <int DIM>
+__host__ __device__ constexpr int box_face_slot(int q, int t) {
+    using B = BoxShape<DIM>;
+    return (B::NSF % B::NP == 0 || t < B::FPT - 1) ? q + B::NP * t
+                                                   : (q >= B::FPT * B::NP - B::NSF ? q + B::NSF - B::NP : -1);
+}
+
 // primitives <-> two float4: 2D (rho, v0, v1, p) (beta, lrho, lbeta, -);
 // 3D (rho, v0, v1, v2) (p, beta, lrho, lbeta)
 // Shared-memory slots.  A warp's 16-byte loads are served eight threads at a
@@ -233,7 +245,11 @@ inline void build_node_table(NodeTable<DIM> &T, int q, const float *Df) {   // h
     }
 #pragma unroll
     for (int t = 0; t < B::FPT; ++t) {
-        const int sl = q + NP * t;
+        const int sl = box_face_slot<DIM>(q, t);
+        if (sl < 0) {
+            T.sfd[t] = 0;
+            continue;
+        }
         const int f = sl / NFP, kk = sl % NFP;
         T.sfd[t] = f | (node_slot<DIM>(face_node_dev<DIM>(f, kk)) << 8) | (face_node_dev<DIM>(f ^ 1, kk) << 16);
     }
@@ -321,7 +337,7 @@ __global__ void __launch_bounds__(EPB * ipow4(DIM), box_min_blocks<DIM, EPB, PIP
         e_out = __ldg(P.elist + (slot < P.n_active ? slot : P.n_active - 1));
 #pragma unroll
         for (int t = 0; t < FPT; ++t)
-            nb_out[t] = (q + NP * t < NSF) ? __ldg(P.nbr + (size_t)e_out * NF + (T.sfd[t] & 0xff)) : e_out;
+            nb_out[t] = (box_face_slot<DIM>(q, t) >= 0) ? __ldg(P.nbr + (size_t)e_out * NF + (T.sfd[t] & 0xff)) : e_out;
     };
     // PIPE: asynchronous copies of a group's per-node data into the staging columns
     auto issue = [&](int e_i, const int (&nb_i)[FPT]) {
@@ -342,7 +358,7 @@ __global__ void __launch_bounds__(EPB * ipow4(DIM), box_min_blocks<DIM, EPB, PIP
             if (P.do_b) cp_async4(&S.st_own[5 * V][tid], P.wJ_f + ix);
 #pragma unroll
             for (int t = 0; t < FPT; ++t) {
-                if (q + NP * t < NSF) {
+                if (box_face_slot<DIM>(q, t) >= 0) {
                     const size_t jn = (size_t)nb_i[t] * NP + (T.sfd[t] >> 16);
 #pragma unroll
                     for (int v = 0; v < V; ++v) {
@@ -400,7 +416,7 @@ __global__ void __launch_bounds__(EPB * ipow4(DIM), box_min_blocks<DIM, EPB, PIP
             cp_async_wait_all();                          // staging columns are thread-private: no barrier
 #pragma unroll
             for (int t = 0; t < FPT; ++t)
-                if (q + NP * t < NSF) row_staged(S.st_nb[t], gnb[t], un[t]);
+                if (box_face_slot<DIM>(q, t) >= 0) row_staged(S.st_nb[t], gnb[t], un[t]);
             row_staged(S.st_own, g, u);
             if (P.d_read) {
 #pragma unroll
@@ -410,7 +426,7 @@ __global__ void __launch_bounds__(EPB * ipow4(DIM), box_min_blocks<DIM, EPB, PIP
         } else {
 #pragma unroll
             for (int t = 0; t < FPT; ++t)
-                if (q + NP * t < NSF)
+                if (box_face_slot<DIM>(q, t) >= 0)
                     stage_row_f<V>(P, NPtot, (size_t)nb_c[t] * NP + (T.sfd[t] >> 16), __ldg(P.gp + nb_c[t]), un[t]);
             stage_row_f<V>(P, NPtot, idx, g, u);
             if (gn < ngroups) group_ids(gn, e_n, nb_n);
@@ -433,8 +449,8 @@ __global__ void __launch_bounds__(EPB * ipow4(DIM), box_min_blocks<DIM, EPB, PIP
         // ---- B: interface fluxes at this element's face nodes
 #pragma unroll
         for (int t = 0; t < FPT; ++t) {
-            const int sl = q + NP * t;
-            if (sl < NSF) {
+            const int sl = box_face_slot<DIM>(q, t);
+            if (sl >= 0) {
                 const int sfd = T.sfd[t];
                 const int f = sfd & 0xff, k = f >> 1, qs = (sfd >> 8) & 0xff;
                 const int qss = qs;   // already a slot
