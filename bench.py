@@ -174,8 +174,8 @@ STAGE_TRAFFIC = {"workload": "batched2d",
                  # last stage, from a capture of the first 128 instances
                  # (inputs well above L2); a launch's traffic scales with its
                  # elements
-                 "bytes_per_element": {1: (771602176 + 558539008) / 763942},   # 128 instances, 0.994 of algorithmic
-                 "sources_sha256": "717167492a36e766833b3ab225069deec51eb76f50b0a9fa1af51fd4c26d2dc4"}
+                 "bytes_per_element": {1: (772116736 + 558081792) / 763942},   # 128 instances, 0.994 of algorithmic
+                 "sources_sha256": "ce2b1d2ff32cc3e15d09a1d873b3b789aa2790eb130441ffe7b9ca772ea26b9a"}
 STAGE_SOURCES = ["stage.cuh", "stage_box.cuh", "physics.cuh", "dfloat.cuh", "kernels_stage2d.cu", "stage_launch.cu"]
 
 
@@ -552,13 +552,45 @@ def run_native(args):
     # a fixed number of steps, independent of --steps: a short pipeline is
     # mostly fill and drain (the first copy in and the last copy out overlap
     # nothing)
+    # the host link's rate on these pinned buffers in this process (untimed,
+    # reported beside e2e: it bounds the pipeline and varies between boxes)
+    link = {}
+    dev_tmp = torch.empty_like(host_u, device=dev)
+    for name, fn in (("h2d", lambda: dev_tmp.copy_(host_u, non_blocking=True)),
+                     ("d2h", lambda: host_out[0].copy_(dev_tmp, non_blocking=True))):
+        fn()
+        torch.cuda.synchronize()
+        t_l = time.perf_counter()
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        link[name + "_gbs"] = 3 * state_bytes / (time.perf_counter() - t_l) / 1e9
+    dev_tmp2 = torch.empty_like(dev_tmp)
+    torch.cuda.synchronize()
+    t_l = time.perf_counter()
+    for _ in range(3):
+        with torch.cuda.stream(streams[0]):
+            dev_tmp.copy_(host_u, non_blocking=True)
+        with torch.cuda.stream(streams[1]):
+            host_out[0].copy_(dev_tmp2, non_blocking=True)
+    torch.cuda.synchronize()
+    link["both_gbs"] = 6 * state_bytes / (time.perf_counter() - t_l) / 1e9
+    del dev_tmp, dev_tmp2
+    # Each step waits for the previous context's step (an event), so the
+    # steps run one after another while the copies, the split and the join of
+    # the other contexts overlap them; left to themselves the three streams
+    # can fall into computing together and then copying together.
     e2e_steps = args.e2e_steps
+    done_ev = [torch.cuda.Event() for _ in range(e2e_steps)]
     t0 = time.perf_counter()
     for k in range(e2e_steps):
         X = k % n_ctx
         sX = streams[X].cuda_stream
         pk.perrk_set_state(ctxs[X].h, host_u.data_ptr(), on_device=pk.STATE_HOST_ASYNC, stream=sX)
+        if k > 0:
+            streams[X].wait_event(done_ev[k - 1])
         pk.perrk_step(ctxs[X].h, 1, info=False, stream=sX)
+        done_ev[k].record(streams[X])
         pk.perrk_get_state(ctxs[X].h, host_out[X].data_ptr(), on_device=pk.STATE_HOST_ASYNC, stream=sX)
     torch.cuda.synchronize()
     e2e_time = reduce_over_ranks(time.perf_counter() - t0, world, "max")
@@ -615,7 +647,7 @@ def run_native(args):
                                                 f"({cpu[2]:.1f} s, one thread)"}},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes,
                 "pipeline": f"{n_ctx} contexts, {n_ctx} streams, asynchronous pinned copies",
-                "results_agree": e2e_match},
+                "results_agree": e2e_match, "host_link": link},
         "phases": phases,
         "gpu_launches": kernels_per_step * args.steps,
         "clocks": clk,
