@@ -46,8 +46,16 @@ DTYPE_CHOSEN = "f32 fluxes/K + f32x2 (~48-bit) state, d, entropy + f64 scalars"
 UNIT = "DOF-stage updates/s"
 
 
-def make_workload(name, rank=0, instances=None):
+def make_workload(name, rank=0, instances=None, size=None):
     import workloads
+    if size and name in ("khi2d", "tgv3d"):
+        # a smaller mesh of the same configuration (profiling captures)
+        if name == "khi2d":
+            return [workloads.khi_2d(n=size, seed=1 + rank)], (f"Kelvin-Helmholtz, {size}x{size} quads graded in y "
+                                                                "(4 levels), N=3, 4 partitions E={16,10,7,5}, p=4, ES")
+        return [workloads.tgv_3d(n=size, n_fine=size // 4)], (f"Taylor-Green vortex Ma 0.1, {size}^3 boxes, central "
+                                                               f"{size // 4} per axis at h/2, N=3, 2 partitions "
+                                                               "E={8,4}, p=3, EC")
     if name == "batched2d":
         insts = workloads.batched_2d(n_inst=256, seed=1 + rank)[:(instances or 256)]
         return insts, ("256 independent 2D Euler instances, n x n quads with n ~ U{16..128} (1.63M elements, "
@@ -387,7 +395,7 @@ def run_native(args):
     stream = torch.cuda.current_stream()
     sh = stream.cuda_stream
 
-    insts, desc = make_workload(args.workload, rank, args.instances)
+    insts, desc = make_workload(args.workload, rank, args.instances, args.size)
     if args.instances:
         desc = f"the first {len(insts)} of: " + desc
     u0 = np.concatenate([w.u0 for w in insts], axis=1)
@@ -726,6 +734,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="batched2d")
+    ap.add_argument("--size", type=int, default=None,
+                    help="khi2d / tgv3d: cells per direction instead of 256 / 64 (smaller cases for profiling)")
     ap.add_argument("--instances", type=int, default=None,
                     help="batched2d: use only the first N instances (profiling on a reduced case)")
     ap.add_argument("--max-it", type=int, default=4)
