@@ -40,11 +40,11 @@ struct BoxShape {
     static constexpr int X = DIM == 3 ? 1 : 0;                // 3D: fifth component beside a float4
 };
 
-// Face slot that thread q takes in face round t (or -1): rounds 0 .. FPT - 2
-// take slot q + NP t; a partial last round (3D: 96 face slots over 64
-// threads) goes to the upper threads, so that it does not fall on the same
-// warps as the partial last round of node pairs (pairs q + NP t go to the
-// lower threads).
+// Face slot that thread q takes in face iteration t (or -1): iterations
+// 0 .. FPT - 2 take slot q + NP t; a partial last iteration (3D: 96 face
+// slots over 64 threads) goes to the upper threads, so that it does not fall
+// on the same warps as the partial last iteration of node pairs (pairs
+// q + NP t go to the lower threads).
 template <int DIM>
 __host__ __device__ constexpr int box_face_slot(int q, int t) {
     using B = BoxShape<DIM>;
