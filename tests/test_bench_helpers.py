@@ -61,3 +61,16 @@ def test_all_cores_oracle_pool_runs_windows():
     finally:
         pool.close()
     assert all(not p.is_alive() for p in pool.procs)
+
+
+def test_make_workload_size_option():
+    """--size gives the same single-mesh configuration on a smaller mesh
+    (profiling captures): cells per direction, partitions and schemes kept."""
+    import bench
+    (k,), _ = bench.make_workload("khi2d", size=16)
+    (t,), _ = bench.make_workload("tgv3d", size=8)
+    assert k.n_elem == 16 * 16 and k.E == [16, 10, 7, 5] and k.order == 4
+    assert t.n_elem == 8 ** 3 and t.E == [8, 4] and t.order == 3
+    assert set(t.part.tolist()) == {0, 1}
+    (b,), _ = bench.make_workload("khi2d")
+    assert b.n_elem == 256 * 256
