@@ -358,17 +358,20 @@ def run_reference(args):
         # each timed step: a window of ref_window seconds in which every host
         # core takes whole oracle steps of its own instances
         pool = OraclePool(insts, 2, cores)
+        # the timed windows of the whole run stay near 150 s whatever --steps
+        # is (a window still completes at least one oracle step per process)
+        window = min(args.ref_window, max(0.5, 150.0 / max(1, args.steps)))
         for _ in range(args.warmup):
-            pool.round(min(1.0, args.ref_window))
+            pool.round(min(1.0, window))
         rates, el = [], 0.0
         for _ in range(args.steps):
-            r, t = pool.round(args.ref_window)
+            r, t = pool.round(window)
             rates.append(r)
             el += t
         pool.close()
         val = float(np.mean(rates))
         used = cores
-        sample = (f"{args.steps} timed windows of {args.ref_window:g} s, in each every one of {cores} host processes "
+        sample = (f"{args.steps} timed windows of {window:g} s, in each every one of {cores} host processes "
                   f"(numpy float64, one thread each, started together at a barrier) takes whole oracle steps of its "
                   f"own instances ({pool.n_inst} instances in all); after {args.warmup} warm-up windows"
                   + (f"; {s_note}" if s_note else ""))
