@@ -739,7 +739,7 @@ perrk_status perrk_stage_info(const perrk_ctx *h, int stage, int64_t *n_active, 
     for (int k = 0; k < na; ++k) {
         const int e = c.elist[k];
         const StageCoef &sc = coef[(size_t)stage * c.n_gp + c.gp_of_elem[e]];
-        int64_t arrays = 1 /*U*/ + 1 /*K out*/;
+        int64_t arrays = 1 /*U*/ + (stage == c.S - 1 ? 0 : 1) /*K out (not stored at the last stage)*/;
         if (stage > 0) arrays += 1;               // K_1
         if (stage > 0 && sc.asub != 0.0) arrays += 1;  // K_{i-1}
         int64_t dbytes = 0;

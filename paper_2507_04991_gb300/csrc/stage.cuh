@@ -57,6 +57,8 @@ struct StageParams {
     float inv_w_f, gm1_f, inv_gm1_f, gam_f;
     uint32_t *flags;
     int ws_stall;               // test hook of the staged 2D box kernel: its producer fills no buffer
+    int k_store;                // store K_i (0 at a step's last stage: K_S enters d from registers and is
+                                // read by no later launch)
     // 2:1 mortars: rows (coarse, face, fine lower, fine upper) of this stage's
     // n_mortar mortars, the trace slot of each element face (or -1; null
     // without mortars), the traces [slot][NFP][V] in kernel precision and the
@@ -493,7 +495,7 @@ __global__ void __launch_bounds__(EPB * ipow4(DIM), stage_min_blocks<DIM, Real, 
             if (EQ == EQ_EULER && v > 0 && kv) Kr[v] = dfma(-acc[v], invJ, kv[(size_t)(v - 1) * NPtot + idx]);
             else Kr[v] = -acc[v] * invJ;
             if (!isfinite(Kr[v])) bad |= PERRK_FLAG_NONFINITE;
-            if (valid) {
+            if (valid && P.k_store) {
                 if constexpr (sizeof(Real) == 8) P.Kout[v * NPtot + idx] = Kr[v];
                 else P.Koutf[v * NPtot + idx] = Kr[v];
             }

@@ -559,7 +559,7 @@ __global__ void __launch_bounds__(EPB * ipow4(DIM), box_min_blocks<DIM, EPB, PIP
             ksum += Kr[v];
         }
         if (!isfinite(ksum)) bad |= PERRK_FLAG_NONFINITE;
-        if (valid) {
+        if (valid && P.k_store) {
 #pragma unroll
             for (int v = 0; v < V; ++v) P.Koutf[v * NPtot + idx] = Kr[v];
         }

@@ -78,6 +78,9 @@ perrk_status launch_stage(Ctx &c, int stage, bool rhs_only, const double *in_u, 
     P.NE = (size_t)c.n_elem;
     P.n_active = rhs_only ? c.n_elem : c.n_active[stage];
     P.stage1 = (stage == 0 || rhs_only) ? 1 : 0;
+    // K_S of a step's last stage enters d from registers and no later launch
+    // reads it (the next step starts from K_1): not stored
+    P.k_store = (rhs_only || stage != c.S - 1) ? 1 : 0;
     P.do_b = (!rhs_only && c.any_b[stage]) ? 1 : 0;
     P.d_read = (!rhs_only && c.d_read[stage]) ? 1 : 0;
     P.d_fused = c.d_fused ? 1 : 0;

@@ -455,7 +455,7 @@ __global__ void __launch_bounds__(ws_threads<EPB, NCG>()) k_stage_ws(const Stage
             ksum += Kr[v];
         }
         if (!isfinite(ksum)) bad |= PERRK_FLAG_NONFINITE;
-        if (valid) {
+        if (valid && P.k_store) {
 #pragma unroll
             for (int v = 0; v < V; ++v) P.Koutf[v * NPtot + idx] = Kr[v];
         }
