@@ -49,6 +49,7 @@ perrk_status cuda_check(int err, const char *what) {
     } while (0)
 #define PERRK_CUDA(x, what) PERRK_TRY(cuda_check((int)(x), what))
 
+// a device copy of a host vector in its own allocation (caller frees)
 template <typename T>
 static perrk_status upload(T *&dst, const std::vector<T> &src, const char *what) {
     if (src.empty()) {
@@ -60,28 +61,96 @@ static perrk_status upload(T *&dst, const std::vector<T> &src, const char *what)
     return PERRK_OK;
 }
 
+// The buffers a context sizes when it is created live in one device
+// allocation (one cudaMalloc, one cudaFree): zero-initialised buffers first
+// (one memset), then the tables copied from the host (one copy from a host
+// staging buffer), then buffers the kernels fill before reading.  Every
+// buffer starts on a 256-byte boundary.
+class ArenaPlan {
+  public:
+    void zeroed(void **slot, size_t bytes) { add(slot, bytes, nullptr, 0); }
+    void raw(void **slot, size_t bytes) { add(slot, bytes, nullptr, 2); }
+    template <typename T>
+    void upload(T *&slot, const std::vector<T> &v) {
+        add(reinterpret_cast<void **>(&slot), v.size() * sizeof(T), v.data(), 1);
+    }
+    perrk_status commit(Ctx &c) {
+        size_t off = 0, zero_end = 0, up0 = 0, up1 = 0;
+        for (int kind = 0; kind < 3; ++kind) {
+            if (kind == 1) up0 = off;
+            for (Item &it : items_)
+                if (it.kind == kind) {
+                    it.offset = off;
+                    off += (it.bytes + 255) / 256 * 256;
+                }
+            if (kind == 0) zero_end = off;
+            if (kind == 1) up1 = off;
+        }
+        c.arena_bytes = off;
+        if (off == 0) return PERRK_OK;
+        PERRK_CUDA(cudaMalloc(&c.arena, off), "context alloc");
+        char *base = static_cast<char *>(c.arena);
+        for (Item &it : items_) *it.slot = base + it.offset;
+        if (zero_end > 0) PERRK_CUDA(cudaMemset(base, 0, zero_end), "context clear");
+        if (up1 > up0) {
+            std::vector<char> staging(up1 - up0, 0);
+            for (const Item &it : items_)
+                if (it.kind == 1) memcpy(staging.data() + (it.offset - up0), it.data.data(), it.bytes);
+            PERRK_CUDA(cudaMemcpy(base + up0, staging.data(), staging.size(), cudaMemcpyHostToDevice), "context upload");
+        }
+        return PERRK_OK;
+    }
+
+  private:
+    struct Item {
+        void **slot;
+        size_t bytes, offset;
+        std::vector<char> data;
+        int kind;   // 0 zeroed, 1 uploaded, 2 raw
+    };
+    void add(void **slot, size_t bytes, const void *src, int kind) {
+        *slot = nullptr;
+        if (bytes == 0) return;
+        Item it{slot, bytes, 0, {}, kind};
+        if (src) it.data.assign(static_cast<const char *>(src), static_cast<const char *>(src) + bytes);
+        items_.push_back(std::move(it));
+    }
+    std::vector<Item> items_;
+};
+
 static void free_ctx(Ctx &c) {
     void *ptrs[] = {c.g_box_tab, c.U, c.K1, c.Ka, c.Kb, c.d, c.Uf, c.Ul, c.dh, c.dl, c.e_dhf, c.g_wJ_lo, c.K1f, c.Kaf, c.Kbf, c.e_dh, c.g_node, c.g_elem, c.g_fnorm, c.g_wJ, c.g_nbr, c.g_gp,
                     c.g_elist, c.g_chunk_inst, c.g_chunk_e0, c.g_chunk_e1, c.g_inst_chunk0, c.g_inst_nchunks,
                     c.g_coef, c.g_coef_f, c.g_scal, c.g_partials, c.g_counters, c.g_flags, c.g_records, c.g_mlp,
                     c.g_dftab, c.g_node_f, c.g_elem_f, c.g_fnorm_f, c.g_wJ_f, c.g_ring, c.visc_fv,
                     c.visc_kv, c.g_mortars, c.g_face_mortar, c.g_mtrace};
-    for (void *p : ptrs)
-        if (p) cudaFree(p);
+    const char *a0 = static_cast<const char *>(c.arena), *a1 = a0 + c.arena_bytes;
+    for (void *p : ptrs)   // buffers allocated on their own later (the MLP weights)
+        if (p && !(c.arena && static_cast<const char *>(p) >= a0 && static_cast<const char *>(p) < a1)) cudaFree(p);
+    if (c.arena) cudaFree(c.arena);
+    c.arena = nullptr;
+    c.arena_bytes = 0;
     if (c.graph_exec) cudaGraphExecDestroy((cudaGraphExec_t)c.graph_exec);
     if (c.graph) cudaGraphDestroy((cudaGraph_t)c.graph);
     c.graph_exec = c.graph = nullptr;
 }
 
-static perrk_status upload_coefficients(Ctx &c) {
+// Stage coefficients of every (stage, global partition) and, with dt_too,
+// each instance's dt in its scalar record (one strided copy).
+static perrk_status upload_coefficients(Ctx &c, bool dt_too = true) {
     std::vector<StageCoef> coef;
     std::vector<StageCoefF> coef_f;
     stage_coefficients(c, coef, coef_f);
     PERRK_CUDA(cudaMemcpy(c.g_coef, coef.data(), coef.size() * sizeof(StageCoef), cudaMemcpyHostToDevice), "coef upload");
     PERRK_CUDA(cudaMemcpy(c.g_coef_f, coef_f.data(), coef_f.size() * sizeof(StageCoefF), cudaMemcpyHostToDevice),
                "coef upload");
-    for (int k = 0; k < c.n_inst; ++k)
-        PERRK_CUDA(cudaMemcpy(&c.g_scal[k].dt, &c.inst[k].dt, sizeof(double), cudaMemcpyHostToDevice), "dt upload");
+    if (dt_too && c.n_inst > 0) {
+        std::vector<double> dts(c.n_inst);
+        for (int k = 0; k < c.n_inst; ++k) dts[k] = c.inst[k].dt;
+        PERRK_CUDA(cudaMemcpy2D(&c.g_scal[0].dt, sizeof(InstScalars), dts.data(), sizeof(double), sizeof(double),
+                                (size_t)c.n_inst, cudaMemcpyHostToDevice),
+                   "dt upload");
+    }
     c.graph_dirty = true;
     return PERRK_OK;
 }
@@ -93,87 +162,77 @@ static perrk_status alloc_ctx(Ctx &c) {
     make_chunks(c, sms);
     const size_t nstate = (size_t)c.V * c.n_elem * c.NP;
     const bool mixed = c.opt.precision == PERRK_MIXED;
+    ArenaPlan A;
     // float64 form: U, K_1, two stage registers, d.  Mixed form: U and d as
     // float pairs (hi, lo), FP32 stage registers, U (float64) as the staging
     // buffer of set_state / get_state.
-    std::vector<double **> dbufs = {&c.U};
-    if (!mixed) dbufs.insert(dbufs.end(), {&c.d, &c.K1, &c.Ka, &c.Kb});
-    for (double **b : dbufs) {
-        PERRK_CUDA(cudaMalloc((void **)b, nstate * sizeof(double)), "state alloc");
-        PERRK_CUDA(cudaMemset(*b, 0, nstate * sizeof(double)), "state clear");
-    }
+    A.zeroed(reinterpret_cast<void **>(&c.U), nstate * sizeof(double));
+    if (!mixed)
+        for (double **b : {&c.d, &c.K1, &c.Ka, &c.Kb}) A.zeroed(reinterpret_cast<void **>(b), nstate * sizeof(double));
     if (mixed) {
-        for (float **b : {&c.Uf, &c.Ul, &c.dh, &c.dl, &c.K1f, &c.Kaf, &c.Kbf}) {
-            PERRK_CUDA(cudaMalloc((void **)b, nstate * sizeof(float)), "state alloc");
-            PERRK_CUDA(cudaMemset(*b, 0, nstate * sizeof(float)), "state clear");
-        }
-        PERRK_CUDA(cudaMalloc((void **)&c.e_dhf, (size_t)c.n_elem * 2 * sizeof(float)), "e_dh alloc");
-        PERRK_CUDA(cudaMemset(c.e_dhf, 0, (size_t)c.n_elem * 2 * sizeof(float)), "e_dh clear");
+        for (float **b : {&c.Uf, &c.Ul, &c.dh, &c.dl, &c.K1f, &c.Kaf, &c.Kbf})
+            A.zeroed(reinterpret_cast<void **>(b), nstate * sizeof(float));
+        A.zeroed(reinterpret_cast<void **>(&c.e_dhf), (size_t)c.n_elem * 2 * sizeof(float));
     } else {
-        PERRK_CUDA(cudaMalloc((void **)&c.e_dh, (size_t)c.n_elem * sizeof(double)), "e_dh alloc");
-        PERRK_CUDA(cudaMemset(c.e_dh, 0, (size_t)c.n_elem * sizeof(double)), "e_dh clear");
+        A.zeroed(reinterpret_cast<void **>(&c.e_dh), (size_t)c.n_elem * sizeof(double));
     }
-    PERRK_TRY(upload(c.g_node, c.geo_node, "geometry"));
-    PERRK_TRY(upload(c.g_elem, c.geo_elem, "geometry"));
-    PERRK_TRY(upload(c.g_fnorm, c.fnorm, "normals"));
-    PERRK_TRY(upload(c.g_wJ, c.wJ, "weights"));
+    A.upload(c.g_node, c.geo_node);
+    A.upload(c.g_elem, c.geo_elem);
+    A.upload(c.g_fnorm, c.fnorm);
+    A.upload(c.g_wJ, c.wJ);
     if (mixed) {
         auto tof = [](const std::vector<double> &v) { return std::vector<float>(v.begin(), v.end()); };
-        PERRK_TRY(upload(c.g_node_f, tof(c.geo_node), "geometry"));
-        PERRK_TRY(upload(c.g_elem_f, tof(c.geo_elem), "geometry"));
-        PERRK_TRY(upload(c.g_fnorm_f, tof(c.fnorm), "normals"));
-        PERRK_TRY(upload(c.g_wJ_f, tof(c.wJ), "weights"));
+        A.upload(c.g_node_f, tof(c.geo_node));
+        A.upload(c.g_elem_f, tof(c.geo_elem));
+        A.upload(c.g_fnorm_f, tof(c.fnorm));
+        A.upload(c.g_wJ_f, tof(c.wJ));
         std::vector<float> wlo(c.wJ.size());
         for (size_t i = 0; i < wlo.size(); ++i) wlo[i] = (float)(c.wJ[i] - (double)(float)c.wJ[i]);
-        PERRK_TRY(upload(c.g_wJ_lo, wlo, "weights"));
+        A.upload(c.g_wJ_lo, wlo);
     }
-    PERRK_TRY(upload(c.g_nbr, c.nbr, "neighbours"));
+    A.upload(c.g_nbr, c.nbr);
     if (c.n_mortars > 0) {
-        PERRK_TRY(upload(c.g_mortars, c.mortars, "mortars"));
-        PERRK_TRY(upload(c.g_face_mortar, c.face_mortar, "mortars"));
+        A.upload(c.g_mortars, c.mortars);
+        A.upload(c.g_face_mortar, c.face_mortar);
         const size_t nt = (size_t)3 * c.n_mortars * ipow4(c.dim - 1) * c.V * (mixed ? sizeof(float) : sizeof(double));
-        PERRK_CUDA(cudaMalloc(&c.g_mtrace, nt), "mortar traces");
-        PERRK_CUDA(cudaMemset(c.g_mtrace, 0, nt), "mortar traces");
+        A.zeroed(&c.g_mtrace, nt);
     }
-    PERRK_TRY(upload(c.g_gp, c.gp_of_elem, "partitions"));
-    PERRK_TRY(upload(c.g_elist, c.elist, "element list"));
+    A.upload(c.g_gp, c.gp_of_elem);
+    A.upload(c.g_elist, c.elist);
     if (c.viscous) {
-        PERRK_TRY(upload(c.g_ring, c.ring, "viscous rings"));
+        A.upload(c.g_ring, c.ring);
         const size_t wsz = mixed ? sizeof(float) : sizeof(double);
         const size_t nn = (size_t)c.n_elem * c.NP * (c.V - 1);
-        PERRK_CUDA(cudaMalloc(&c.visc_fv, nn * c.dim * wsz), "viscous alloc");
-        PERRK_CUDA(cudaMalloc(&c.visc_kv, nn * wsz), "viscous alloc");
-        PERRK_CUDA(cudaMemset(c.visc_fv, 0, nn * c.dim * wsz), "viscous clear");
-        PERRK_CUDA(cudaMemset(c.visc_kv, 0, nn * wsz), "viscous clear");
+        A.zeroed(&c.visc_fv, nn * c.dim * wsz);
+        A.zeroed(&c.visc_kv, nn * wsz);
     }
-    PERRK_TRY(upload(c.g_chunk_inst, c.chunk_inst, "chunks"));
-    PERRK_TRY(upload(c.g_chunk_e0, c.chunk_e0, "chunks"));
-    PERRK_TRY(upload(c.g_chunk_e1, c.chunk_e1, "chunks"));
+    A.upload(c.g_chunk_inst, c.chunk_inst);
+    A.upload(c.g_chunk_e0, c.chunk_e0);
+    A.upload(c.g_chunk_e1, c.chunk_e1);
     std::vector<int32_t> ic0(c.n_inst), inc(c.n_inst);
     for (int k = 0; k < c.n_inst; ++k) {
         ic0[k] = c.inst[k].chunk0;
         inc[k] = c.inst[k].n_chunks;
     }
-    PERRK_TRY(upload(c.g_inst_chunk0, ic0, "chunks"));
-    PERRK_TRY(upload(c.g_inst_nchunks, inc, "chunks"));
-    PERRK_CUDA(cudaMalloc((void **)&c.g_coef, (size_t)c.S * c.n_gp * sizeof(StageCoef)), "coef alloc");
-    PERRK_CUDA(cudaMalloc((void **)&c.g_coef_f, (size_t)c.S * c.n_gp * sizeof(StageCoefF)), "coef alloc");
+    A.upload(c.g_inst_chunk0, ic0);
+    A.upload(c.g_inst_nchunks, inc);
+    A.raw(reinterpret_cast<void **>(&c.g_coef), (size_t)c.S * c.n_gp * sizeof(StageCoef));      // upload_coefficients
+    A.raw(reinterpret_cast<void **>(&c.g_coef_f), (size_t)c.S * c.n_gp * sizeof(StageCoefF));
     std::vector<InstScalars> scal(c.n_inst);
     for (auto &s : scal) {
         memset(&s, 0, sizeof s);
         s.gamma = 1.0;
         for (int k = 0; k < 3; ++k) s.hist_gamma[k] = 1.0;
     }
-    PERRK_TRY(upload(c.g_scal, scal, "scalars"));
-    PERRK_CUDA(cudaMalloc((void **)&c.g_partials, c.chunk_inst.size() * 8 * sizeof(double)), "partials alloc");
-    PERRK_CUDA(cudaMalloc((void **)&c.g_counters, (size_t)c.n_inst * sizeof(uint32_t)), "counters alloc");
-    PERRK_CUDA(cudaMemset(c.g_counters, 0, (size_t)c.n_inst * sizeof(uint32_t)), "counters clear");
-    PERRK_CUDA(cudaMalloc((void **)&c.g_flags, sizeof(uint32_t)), "flags alloc");
-    PERRK_CUDA(cudaMemset(c.g_flags, 0, sizeof(uint32_t)), "flags clear");
+    for (int k = 0; k < c.n_inst; ++k) scal[k].dt = c.inst[k].dt;
+    A.upload(c.g_scal, scal);
+    A.raw(reinterpret_cast<void **>(&c.g_partials), c.chunk_inst.size() * 8 * sizeof(double));
+    A.zeroed(reinterpret_cast<void **>(&c.g_counters), (size_t)c.n_inst * sizeof(uint32_t));
+    A.zeroed(reinterpret_cast<void **>(&c.g_flags), sizeof(uint32_t));
     {
         std::vector<float> tab, consts;
         df_tables(c.gamma_gas, tab, consts);
-        PERRK_TRY(upload(c.g_dftab, tab, "df table"));
+        A.upload(c.g_dftab, tab);
         for (int i = 0; i < 8; ++i) c.df_consts[i] = consts[i];
     }
     if (mixed && c.equation != PERRK_BURGERS_1D && !c.curved && c.dim >= 2) {
@@ -183,11 +242,12 @@ static perrk_status alloc_ctx(Ctx &c) {
         std::vector<uint8_t> tab(nb);
         if (c.dim == 2) box_node_table_2d(Df, tab.data());
         else box_node_table_3d(Df, tab.data());
-        PERRK_TRY(upload(*reinterpret_cast<uint8_t **>(&c.g_box_tab), tab, "box table"));
+        A.upload(*reinterpret_cast<uint8_t **>(&c.g_box_tab), tab);
     }
     c.rec_cap = 256;
-    PERRK_CUDA(cudaMalloc((void **)&c.g_records, (size_t)c.rec_cap * c.n_inst * sizeof(perrk_step_info)), "records");
-    return upload_coefficients(c);
+    A.raw(reinterpret_cast<void **>(&c.g_records), (size_t)c.rec_cap * c.n_inst * sizeof(perrk_step_info));
+    PERRK_TRY(A.commit(c));
+    return upload_coefficients(c, false);   // (each instance's dt is in its uploaded scalar record)
 }
 
 static perrk_status enqueue_step(Ctx &c, cudaStream_t st) {
