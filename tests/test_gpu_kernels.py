@@ -61,6 +61,12 @@ def test_autotune_keeps_results_bitwise(precision):
     s2.close()
     assert tuning["elems_per_cta"] in (4, 8, 16) and tuning["relax_threads"] in (128, 256)
     assert tuning["stage_variant"] in (0, 1, 2, 3, 4)
+    # grid candidates: one CTA per element group, 2, 4 or 8 CTAs per SM, and
+    # for the box kernels (mixed form) the one-wave grids of 20, 10, 5 per SM
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    per_sm = (2, 4, 8) + ((5, 10, 20) if precision == pk.MIXED else ())
+    assert tuning["persistent_grid"] in [0] + [k * sms for k in per_sm]
     assert np.array_equal(u1, u2)
     assert [a[0]["gamma"] for a in r1] == [a[0]["gamma"] for a in r2]
 
