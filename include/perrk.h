@@ -382,12 +382,14 @@ perrk_status perrk_entropy(perrk_ctx *ctx, double *H, void *stream);
 
 /* Enqueue exactly one stage kernel (stage index 0..S-1, 0-based) of the
  * step on the context's current buffers (for timing and profiling; the
- * result is the stage's K_i).  Asynchronous on stream. */
+ * result is the stage's K_i, which the last stage keeps in registers only:
+ * it enters d there and nothing reads it later).  Asynchronous on stream. */
 perrk_status perrk_launch_stage(perrk_ctx *ctx, int stage, void *stream);
 
 /* Static facts of one stage launch: elements evaluated and the algorithmic
  * bytes it must move (own-element reads of U_n, K_1, K_{i-1} as the stage
- * rows require, the K_i write, the d read/write at stages with b_i != 0,
+ * rows require, the K_i write (not at the last stage), the d read/write at
+ * stages with b_i != 0,
  * geometry and index data; neighbour face reads are not counted; with
  * viscous terms also the BR1 node fluxes of the gradient set and their
  * divergence).  Also the
