@@ -159,6 +159,7 @@ static perrk_status alloc_ctx(Ctx &c) {
     int dev = 0, sms = 152;
     PERRK_CUDA(cudaGetDevice(&dev), "device query");
     PERRK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "device query");
+    c.sm_count = sms;
     make_chunks(c, sms);
     const size_t nstate = (size_t)c.V * c.n_elem * c.NP;
     const bool mixed = c.opt.precision == PERRK_MIXED;

@@ -192,27 +192,12 @@ __device__ void accept_gamma(InstScalars &s) {
     }
 }
 
-template <int DIM, int EQ>
-__global__ void k_relax_init(const RelaxParams P) {
-    const int chunk = blockIdx.x;
-    const int inst = P.chunk_inst[chunk];
-    double s[1] = {0.0}, c[1] = {0.0}, tot[1];
-    if (P.mixed) {
-        // mixed form: Delta H carries FP32 rounding; double-float block sum on the FP32 pipe
-        df r = {0.0f, 0.0f};
-        float g = 0.0f, a = 0.0f;
-        for (int e = P.chunk_e0[chunk] + threadIdx.x; e < P.chunk_e1[chunk]; e += blockDim.x)
-            r = df_add(r, df{P.e_dhf[2 * e], P.e_dhf[2 * e + 1]});
-        block_sum_df(r, g, a);
-        s[0] = (double)r.hi;
-        c[0] = (double)r.lo;
-        if (!chunk_publish<1>(P, chunk, inst, s, c, tot)) return;
-    } else {
-        for (int e = P.chunk_e0[chunk] + threadIdx.x; e < P.chunk_e1[chunk]; e += blockDim.x) comp_add(s[0], c[0], P.e_dh[e]);
-        if (!chunk_finish<1>(P, chunk, inst, s, c, tot)) return;
-    }
+// The instance's Delta H, the features of the learned guess and the initial
+// gamma of its root solve, from the total of its element Delta H sums
+// (thread 0 of the block that holds the total)
+__device__ void init_instance(const RelaxParams &P, int inst, double tot) {
     InstScalars &S = P.scal[inst];
-    S.dH = S.dt * tot[0];
+    S.dH = S.dt * tot;
     S.feat[0] = S.hist_gamma[0] - 1.0;
     S.feat[1] = S.hist_gamma[1] - 1.0;
     S.feat[2] = S.hist_gamma[2] - 1.0;
@@ -244,6 +229,53 @@ __global__ void k_relax_init(const RelaxParams P) {
         S.done = 1;
         accept_gamma(S);
     }
+}
+
+template <int DIM, int EQ>
+__global__ void k_relax_init(const RelaxParams P) {
+    const int chunk = blockIdx.x;
+    const int inst = P.chunk_inst[chunk];
+    double s[1] = {0.0}, c[1] = {0.0}, tot[1];
+    if (P.mixed) {
+        // mixed form: Delta H carries FP32 rounding; double-float block sum on the FP32 pipe
+        df r = {0.0f, 0.0f};
+        float g = 0.0f, a = 0.0f;
+        for (int e = P.chunk_e0[chunk] + threadIdx.x; e < P.chunk_e1[chunk]; e += blockDim.x)
+            r = df_add(r, df{P.e_dhf[2 * e], P.e_dhf[2 * e + 1]});
+        block_sum_df(r, g, a);
+        s[0] = (double)r.hi;
+        c[0] = (double)r.lo;
+        if (!chunk_publish<1>(P, chunk, inst, s, c, tot)) return;
+    } else {
+        for (int e = P.chunk_e0[chunk] + threadIdx.x; e < P.chunk_e1[chunk]; e += blockDim.x) comp_add(s[0], c[0], P.e_dh[e]);
+        if (!chunk_finish<1>(P, chunk, inst, s, c, tot)) return;
+    }
+    init_instance(P, inst, tot[0]);
+}
+
+// One block per instance (contexts with at least as many instances as SMs,
+// where one block per work chunk is mostly launch overhead): the block sums
+// all element Delta H values of its instance in a fixed order, with no
+// cross-block partials, and sets the instance up.
+__global__ void __launch_bounds__(256) k_relax_init_inst(const RelaxParams P) {
+    const int inst = blockIdx.x;
+    const int c0 = P.inst_chunk0[inst], nc = P.inst_nchunks[inst];
+    const int e0 = P.chunk_e0[c0], e1 = P.chunk_e1[c0 + nc - 1];
+    double tot;
+    if (P.mixed) {
+        df r = {0.0f, 0.0f};
+        float g = 0.0f, a = 0.0f;
+        for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) r = df_add(r, df{P.e_dhf[2 * e], P.e_dhf[2 * e + 1]});
+        block_sum_df(r, g, a);
+        tot = (double)r.hi + (double)r.lo;
+    } else {
+        double sc[1] = {0.0}, cc[1] = {0.0};
+        for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) comp_add(sc[0], cc[0], P.e_dh[e]);
+        __shared__ double sm0[2 * 32];
+        block_sum<1>(sc, cc, sm0);
+        tot = sc[0] + cc[0];
+    }
+    if (threadIdx.x == 0) init_instance(P, inst, tot);
 }
 
 template <int DIM, int EQ, bool DF>
@@ -714,7 +746,10 @@ perrk_status launch_df_log(const float *tab, const float *consts, const double *
 
 perrk_status launch_relax_init(Ctx &c, void *stream) {
     RelaxParams P = relax_params(c);
-    run_init(c, P, (cudaStream_t)stream, 256);
+    if (c.n_inst >= c.sm_count && c.sm_count > 0)
+        k_relax_init_inst<<<c.n_inst, 256, 0, (cudaStream_t)stream>>>(P);
+    else
+        run_init(c, P, (cudaStream_t)stream, 256);
     return cuda_check((int)cudaGetLastError(), "relax_init launch");
 }
 

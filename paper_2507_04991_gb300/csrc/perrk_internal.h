@@ -168,6 +168,7 @@ struct Ctx {
     float *g_dftab = nullptr;                 // double-float log table [129][4]
     void *g_box_tab = nullptr;                // box stage kernels: per-node work table
     float df_consts[8] = {0};                 // log 2, (unused), gamma-1, gamma (float pairs)
+    int sm_count = 0;                         // SMs of the device the context was created on
     void *arena = nullptr;                    // one device allocation holding the buffers sized at create
     size_t arena_bytes = 0;
     int mlp_on = 0;
